@@ -1,0 +1,300 @@
+"""Benchmark: PCG generalized Poisson solve on the 128^3 periodic workload.
+
+One step = one complete solve through the C ABI (gps_gpe_solve): setup of
+s, sqrt(eps) and q, then Algorithm 2 to ||r||_2 <= 1e-10, FP64, inputs
+resident in HBM.  The metric is PCG grid-point iterations per second
+(grid points x PCG iterations / solve time), aggregated over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the reference implementation of the
+method written for the tests) on the host cores, each step a bounded sample
+of the same workload: setup plus a fixed number of PCG iterations.
+
+Under torchrun each rank solves its own replica of the workload on its own
+GPU (the solve does not shard; "replicas only"), timing is the max over
+ranks, and the value is the total over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "gpe_periodic_128"
+METRIC = "PCG grid-pt*iter/s (GPe, periodic 128^3, FP64, ||r|| <= 1e-10)"
+UNIT = "grid-pt*iter/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def config_dict(extra=None):
+    d = {"workload": WORKLOAD, "grid": [128, 128, 128], "h_bohr": 0.3, "bc": "periodic",
+         "charges": 20, "eps0": 78.36, "tol_abs": 1e-10, "problem": "generalized Poisson",
+         "l2_flush": "512 MiB buffer written between timed steps", "parallelism": "replicas"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# FP64 FMA units: 152 SMs x 2 DFMA/clk (measured 600 GFMA/s on this GPU) at
+# the 2070 MHz maximum SM clock, 2 flop per FMA.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def z_pass_flops(P):
+    """Conventional FFT flop count of one z-pass launch: per column a forward
+    and an inverse complex FFT of length Pz (5 L log2 L each) plus the real
+    multiply by the Green's table (2 L)."""
+    import math
+    L = P["Pz"]
+    cols = P["Hx"] * P["Py"]
+    return cols * (2 * 5 * L * math.log2(L) + 2 * L)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_1509_00680_gb300 import build
+    import synth
+
+    build.build()
+    from paper_1509_00680_gb300 import gps
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    p = synth.workload(2)
+    g = gps.grid_from(p.grid)
+    npts = p.grid.npts
+    rho = torch.from_numpy(p.rho.ravel()).to(dev)
+    eps = torch.from_numpy(p.eps.ravel()).to(dev)
+    phi = torch.empty_like(rho)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = gps.Context(local)
+    opts = gps.default_opts(tol_abs=1e-10)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ctx.gpe_solve(g, rho, eps, phi, opts)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.set_profiling(True)
+    ctx.get_profile(reset=True)
+    launches0 = gps.kernel_launches()
+    t_steps, iters = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)                      # evict L2 between steps (not timed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = ctx.gpe_solve(g, rho, eps, phi, opts)
+        e1.record(stream)
+        e1.synchronize()
+        t_steps.append(e0.elapsed_time(e1))
+        iters.append(rep.iters)
+    barrier()
+    launches = gps.kernel_launches() - launches0
+    prof = ctx.get_profile(reset=True)
+    ctx.set_profiling(False)
+    clk = clocks.stop()
+    total_ms = sum(t_steps)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = npts * sum(iters) * ws
+    value = units / (total_ms / 1e3)
+
+    # end-to-end through the host-pointer entry point (copies in the timed region)
+    rho_h = torch.from_numpy(p.rho.ravel().copy()).pin_memory().numpy()
+    eps_h = torch.from_numpy(p.eps.ravel().copy()).pin_memory().numpy()
+    phi_h = torch.empty(npts, dtype=torch.float64).pin_memory().numpy()
+    ctx.gpe_solve_host(g, rho_h, eps_h, phi_h, opts)
+    e2e_ms, e2e_iters = 0.0, 0
+    for _ in range(max(3, args.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = ctx.gpe_solve_host(g, rho_h, eps_h, phi_h, opts)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_iters += rep.iters
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    P = {"Pz": 128, "Py": 128, "Hx": 65}
+    kinds = {k: v for k, v in prof.items() if v[0] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][1])
+    n_l, t_l = kinds[dom]
+    avg_ms = t_l / n_l
+    share = t_l / sum(v[1] for v in kinds.values())
+    roof = {"kernel": dom, "avg_launch_ms": avg_ms, "share_of_kernel_time": share}
+    if dom == "z":
+        fl = z_pass_flops(P)
+        ach = fl / (avg_ms / 1e3) / 1e12
+        roof.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64)"})
+    else:
+        roof.update({"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": None, "traffic": None})
+    roof["per_kernel_ms"] = {k: round(v[1] / max(v[0], 1), 5) for k, v in kinds.items()}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict({"pcg_iters_per_solve": int(statistics.median(iters))}),
+        "solves_per_s": ws * args.steps / (total_ms / 1e3),
+        "e2e": {"value": npts * e2e_iters / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": 2 * npts * 8, "d2h_bytes_per_step": npts * 8},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def oracle_sample(p, iters):
+    """Setup plus `iters` PCG iterations of the oracle on the workload; returns
+    (seconds, iterations)."""
+    import oracle
+    from oracle.operators import Fields
+    from oracle.pcg import neutralize, pcg
+    t0 = time.perf_counter()
+    f = Fields(p.grid, p.eps)
+    rho, _ = neutralize(p.rho, p.grid)
+    _, info = pcg(f, rho, tol_abs=1e-10, max_iter=iters)
+    return time.perf_counter() - t0, info["iters"]
+
+
+def cpu_baseline(p, iters=40):
+    secs, it = oracle_sample(p, iters)
+    return {"value": p.grid.npts * it / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "oracle setup + %d PCG iterations of the 128^3 periodic workload (%.1f s)" % (it, secs)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import synth
+    p = synth.workload(2)
+    iters = 8
+    for _ in range(args.warmup):
+        oracle_sample(p, 2)
+    secs, its = 0.0, 0
+    for _ in range(args.steps):
+        s, i = oracle_sample(p, iters)
+        secs += s
+        its += i
+    value = p.grid.npts * its / secs
+    sample = "per step: oracle setup + %d PCG iterations of the 128^3 periodic workload" % iters
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_dict(),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * gps.h -- C ABI of the GB300 generalized Poisson / Poisson-Boltzmann solver.
+ *
+ * Method: arXiv:1509.00680 (Fisicaro, Genovese, Andreussi, Marzari, Goedecker),
+ * "A generalized Poisson and Poisson-Boltzmann solver for electrostatic
+ * environments".  The solver computes phi with
+ *     div eps grad phi = -4 pi (rho + rho_ions[phi])        (Eqs. GPe, PBe)
+ * by the preconditioned conjugate gradient of Algorithm 2, whose
+ * preconditioner is one vacuum Poisson solve (Eq. PCGdef) and whose operator
+ * is applied through the identity of Eq. (corr) / (corrPB); the nonlinear
+ * Poisson-Boltzmann case adds the ionic-charge outer loop of Algorithm 4.
+ *
+ * Conventions
+ *   Atomic units (bohr, Hartree, e = 1), Gaussian 4 pi as in the paper.
+ *   Fields are contiguous IEEE double arrays of nx*ny*nz points with x
+ *   fastest: index i + nx*(j + ny*k), point (origin + i hx, j hy, k hz).
+ *   "_dev" pointers are CUDA device pointers on the context's device; the
+ *   caller owns them, the library never frees or retains them after a call.
+ *   "_host" entry points take host pointers and copy through library-owned
+ *   device buffers.  Calls are ordered on the given CUDA stream (NULL = the
+ *   legacy default stream) and return after the result is complete on the
+ *   host side (the reports carry host-read scalars).
+ *   A context is not thread safe: one host thread per context.
+ *   Every entry point returns a gps_status; nothing is thrown across the ABI.
+ */
+#ifndef GPS_H
+#define GPS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GPS_OK = 0,
+  GPS_ERR_INVALID = 1,        /* bad argument: sizes, pointer, eps <= 0, unsupported size */
+  GPS_ERR_NOMEM = 2,          /* device allocation failed or the HBM budget is exceeded */
+  GPS_ERR_NOT_CONVERGED = 3,  /* max_iter / max_outer reached; phi holds the last iterate */
+  GPS_ERR_BREAKDOWN = 4,      /* (p, A p) >= 0 or not finite: the operator is not negative definite */
+  GPS_ERR_TIMEOUT = 5,        /* a bounded device wait gave up */
+  GPS_ERR_CUDA = 6,           /* a CUDA runtime call failed */
+  GPS_PENDING = 7             /* asynchronous request not finished yet */
+} gps_status;
+
+typedef enum {
+  GPS_BC_FREE = 0,       /* isolated system: truncated-Coulomb vacuum kernel on a 2x padded grid */
+  GPS_BC_PERIODIC = 1,   /* periodic cell: spectral 4 pi / k^2 kernel */
+  GPS_BC_SURFACE = 2     /* periodic in x and y, free in z (2x padded in z) */
+} gps_bc;
+
+typedef enum { GPS_FP64 = 0, GPS_MIXED = 1 } gps_precision;
+typedef enum { GPS_GPE = 0, GPS_LPB = 1, GPS_NLPB = 2 } gps_problem;
+typedef enum { GPS_OUTER_NEWTON = 0, GPS_OUTER_PRINTED = 1 } gps_outer_mode;
+
+/* Uniform orthorhombic grid.  nx, ny, nz >= 4; each padded FFT length
+ * (2n on free axes, n on periodic axes) must factor into 2, 3 and 5, be even
+ * and be at most 4096.  Sec. "Numerical results" (orthorhombic grid of
+ * uniform spacing). */
+typedef struct {
+  int nx, ny, nz;
+  double hx, hy, hz;
+  int bc;                /* gps_bc */
+} gps_grid;
+
+/* Mobile ions (Eqs. rhoions, ionsconcPB).  Species i has valence z[i] and
+ * bulk concentration c_molar[i] (mol/L).  The ion-exclusion function is the
+ * cavity function gamma = (eps - 1)/(eps0 - 1), so ions live in the solvent
+ * only.  The linear PB term of Eq. (corrPB) is lambda(r) = gamma(r) * 4 pi
+ * sum_i z_i^2 n_i / kT with n_i the number densities in bohr^-3. */
+#define GPS_MAX_SPECIES 8
+typedef struct {
+  int nspecies;
+  int z[GPS_MAX_SPECIES];
+  double c_molar[GPS_MAX_SPECIES];
+  double temperature;    /* K */
+  double eps0;           /* bulk dielectric constant of the solvent (for gamma) */
+} gps_electrolyte;
+
+/* Solver options.  Convergence of Algorithm 2 is tested on the Euclidean norm
+ * of the residual r (Sec. "Preconditioned conjugate gradient"):
+ * ||r||_2 <= max(tol_abs, tol_rel * ||r_0||_2), r_0 = -4 pi rho.
+ * For GPS_NLPB the outer loop stops when the Euclidean norm of the ionic
+ * charge residual falls below tol_outer. */
+typedef struct {
+  double tol_abs;        /* absolute residual tolerance (e.g. 1e-10) */
+  double tol_rel;        /* relative residual tolerance (0 = off) */
+  int max_iter;          /* PCG iterations per solve (inner solves for NLPB) */
+  int max_outer;         /* NLPB outer steps */
+  double tol_outer;      /* NLPB outer tolerance on the ionic-charge residual */
+  double eta;            /* NLPB mixing parameter (printed Algorithm 4) */
+  int outer_mode;        /* gps_outer_mode */
+  double forcing;        /* NLPB Newton: relative inner tolerance cap (e.g. 1e-2) */
+  int precision;         /* gps_precision */
+  double mixed_switch;   /* GPS_MIXED: FP64 preconditioner until ||r|| <= mixed_switch*||r_0|| */
+} gps_opts;
+
+typedef struct {
+  int status;            /* gps_status of the solve */
+  int iters;             /* PCG iterations (summed over inner solves for NLPB) */
+  int outer_iters;       /* NLPB outer steps */
+  int fp64_iters;        /* iterations that used the FP64 preconditioner */
+  double res0;           /* ||r_0||_2 of the (last) PCG */
+  double res;            /* ||r||_2 at exit of the (last) PCG */
+  double outer_res;      /* NLPB: final ionic-charge residual */
+  double background;     /* periodic GPe: mean of rho removed to neutralize the cell */
+  double time_ms;        /* wall time of the call (host clock, synchronized) */
+} gps_report;
+
+typedef struct gps_ctx gps_ctx;
+
+/* Fill *opts with defaults: tol_abs 1e-10, tol_rel 0, max_iter 500,
+ * max_outer 100, tol_outer 1e-10, eta 0.6, Newton outer mode, forcing 1e-2,
+ * FP64, mixed_switch 1e-2. */
+void gps_default_opts(gps_opts* opts);
+
+/* Human-readable name of a status code (static storage). */
+const char* gps_status_string(int status);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * device memory the context keeps in cached plans (0 = no cap).  Returns
+ * GPS_ERR_INVALID for a NULL out pointer or bad device, GPS_ERR_CUDA if the
+ * device cannot be selected. */
+int gps_create(gps_ctx** out, int device, size_t hbm_budget_bytes);
+
+/* Release every plan and buffer of the context (NULL is a no-op). */
+void gps_destroy(gps_ctx* ctx);
+
+/* Device bytes held by the context's cached plans. */
+size_t gps_bytes_in_use(const gps_ctx* ctx);
+
+/* Generalized Poisson equation, Eq. (GPe), by Algorithm 2 from phi_0 = 0.
+ * rho_dev, eps_dev: inputs (eps > 0 everywhere, else GPS_ERR_INVALID);
+ * phi_dev: output.  Periodic BC: the mean of rho is removed (reported in
+ * rep->background) and phi satisfies sum sqrt(eps) phi = 0.  rep may be NULL. */
+int gps_gpe_solve(gps_ctx* ctx, const gps_grid* grid, const double* rho_dev,
+                  const double* eps_dev, double* phi_dev, const gps_opts* opts,
+                  gps_report* rep, void* cuda_stream);
+
+/* Poisson-Boltzmann.  kind = GPS_LPB: linear PB, Eq. (corrPB), by Algorithm 2.
+ * kind = GPS_NLPB: nonlinear PB, Eqs. (PBe, rhoions, ionsconcPB), by the
+ * outer loop of Algorithm 4 (opts->outer_mode selects the printed linear
+ * mixing or the Newton-linearized inner operator), each inner solve by
+ * Algorithm 2.  kind = GPS_GPE ignores the electrolyte. */
+int gps_pb_solve(gps_ctx* ctx, const gps_grid* grid, const double* rho_dev,
+                 const double* eps_dev, const gps_electrolyte* el, int kind,
+                 double* phi_dev, const gps_opts* opts, gps_report* rep,
+                 void* cuda_stream);
+
+/* Same as gps_gpe_solve / gps_pb_solve with host arrays: rho and eps are
+ * copied to library-owned device buffers, phi is copied back. */
+int gps_gpe_solve_host(gps_ctx* ctx, const gps_grid* grid, const double* rho_host,
+                       const double* eps_host, double* phi_host, const gps_opts* opts,
+                       gps_report* rep, void* cuda_stream);
+int gps_pb_solve_host(gps_ctx* ctx, const gps_grid* grid, const double* rho_host,
+                      const double* eps_host, const gps_electrolyte* el, int kind,
+                      double* phi_host, const gps_opts* opts, gps_report* rep,
+                      void* cuda_stream);
+
+/* Step S1 (Eq. corr): s = eps^-1/2 and q = sqrt(eps) lap sqrt(eps) -- the
+ * order-16 finite-difference Laplacian (Sec. "Numerical results") for free
+ * and surface BC, the spectral Laplacian that the vacuum solve inverts for
+ * periodic BC.  s_dev, q_dev: outputs of nx*ny*nz doubles. */
+int gps_setup_fields(gps_ctx* ctx, const gps_grid* grid, const double* eps_dev,
+                     double* s_dev, double* q_dev, void* cuda_stream);
+
+/* Vacuum Poisson solve w = S(sigma), lap w = -4 pi sigma (Eq. SPe) under the
+ * grid's BC.  Periodic BC drops the mean of sigma. */
+int gps_vacuum_solve(gps_ctx* ctx, const gps_grid* grid, const double* sigma_dev,
+                     double* w_dev, void* cuda_stream);
+
+/* Step S3, the preconditioner of Eq. (PCGdef): v = s S(s r) for a given
+ * s = eps^-1/2.  precision = GPS_MIXED runs the FFT passes in FP32. */
+int gps_precondition(gps_ctx* ctx, const gps_grid* grid, const double* s_dev,
+                     const double* r_dev, double* v_dev, int precision,
+                     void* cuda_stream);
+
+/* Ionic charge of Eqs. (rhoions, ionsconcPB) with the cavity exclusion
+ * function: out = gamma sum_i z_i n_i exp(-z_i phi / kT), exponent capped at
+ * +40.  Inputs phi_dev, eps_dev; output out_dev. */
+int gps_ionic_charge(gps_ctx* ctx, const gps_grid* grid, const double* phi_dev,
+                     const double* eps_dev, const gps_electrolyte* el,
+                     double* out_dev, void* cuda_stream);
+
+/* Instrumentation.  With profiling on, every kernel that the solve entry
+ * points launch is bracketed by CUDA events on the call's stream; the
+ * elapsed times are collected when the call returns.  Kernel kinds:
+ * 0 x_fwd, 1 y_fwd, 2 z (forward, Green's multiply, inverse), 3 y_inv,
+ * 4 x_inv, 5 update_p, 6 update_r, 7 setup and other.
+ * gps_get_profile writes per kind the launch count and total milliseconds
+ * accumulated since the last reset (arrays of GPS_PROFILE_KINDS entries). */
+#define GPS_PROFILE_KINDS 8
+int gps_set_profiling(gps_ctx* ctx, int enabled);
+int gps_get_profile(gps_ctx* ctx, long long* launches, double* total_ms, int reset);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+unsigned long long gps_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPS_H */

@@ -1,0 +1,295 @@
+"""Thin ctypes binding of libgps.so (include/gps.h).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  Device arrays are torch CUDA tensors (contiguous float64 on the
+context's device); the *_host entry points take contiguous float64 numpy
+arrays.  The library must have been built (``build.build()``); importing
+this module without it raises -- there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+GPS_OK, GPS_ERR_INVALID, GPS_ERR_NOMEM, GPS_ERR_NOT_CONVERGED = 0, 1, 2, 3
+GPS_ERR_BREAKDOWN, GPS_ERR_TIMEOUT, GPS_ERR_CUDA, GPS_PENDING = 4, 5, 6, 7
+GPS_BC_FREE, GPS_BC_PERIODIC, GPS_BC_SURFACE = 0, 1, 2
+GPS_FP64, GPS_MIXED = 0, 1
+GPS_GPE, GPS_LPB, GPS_NLPB = 0, 1, 2
+GPS_OUTER_NEWTON, GPS_OUTER_PRINTED = 0, 1
+GPS_MAX_SPECIES = 8
+KIND = {"gpe": GPS_GPE, "lpb": GPS_LPB, "nlpb": GPS_NLPB}
+
+
+class gps_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
+                ("bc", ctypes.c_int)]
+
+
+class gps_electrolyte(ctypes.Structure):
+    _fields_ = [("nspecies", ctypes.c_int), ("z", ctypes.c_int * GPS_MAX_SPECIES),
+                ("c_molar", ctypes.c_double * GPS_MAX_SPECIES),
+                ("temperature", ctypes.c_double), ("eps0", ctypes.c_double)]
+
+
+class gps_opts(ctypes.Structure):
+    _fields_ = [("tol_abs", ctypes.c_double), ("tol_rel", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
+                ("tol_outer", ctypes.c_double), ("eta", ctypes.c_double),
+                ("outer_mode", ctypes.c_int), ("forcing", ctypes.c_double),
+                ("precision", ctypes.c_int), ("mixed_switch", ctypes.c_double)]
+
+
+class gps_report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("fp64_iters", ctypes.c_int), ("res0", ctypes.c_double), ("res", ctypes.c_double),
+                ("outer_res", ctypes.c_double), ("background", ctypes.c_double),
+                ("time_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "gps_default_opts": (None, [ctypes.POINTER(gps_opts)]),
+    "gps_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gps_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_size_t]),
+    "gps_destroy": (None, [_P]),
+    "gps_bytes_in_use": (ctypes.c_size_t, [_P]),
+    "gps_gpe_solve": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P,
+                                     ctypes.POINTER(gps_opts), ctypes.POINTER(gps_report), _P]),
+    "gps_pb_solve": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P,
+                                    ctypes.POINTER(gps_electrolyte), ctypes.c_int, _P,
+                                    ctypes.POINTER(gps_opts), ctypes.POINTER(gps_report), _P]),
+    "gps_gpe_solve_host": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P,
+                                          ctypes.POINTER(gps_opts), ctypes.POINTER(gps_report), _P]),
+    "gps_pb_solve_host": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P,
+                                         ctypes.POINTER(gps_electrolyte), ctypes.c_int, _P,
+                                         ctypes.POINTER(gps_opts), ctypes.POINTER(gps_report), _P]),
+    "gps_setup_fields": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P, _P]),
+    "gps_vacuum_solve": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P]),
+    "gps_precondition": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P, ctypes.c_int, _P]),
+    "gps_ionic_charge": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P,
+                                        ctypes.POINTER(gps_electrolyte), _P, _P]),
+    "gps_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gps_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "gps_kernel_launches": (ctypes.c_ulonglong, []),
+}
+GPS_PROFILE_KINDS = 8
+PROFILE_KINDS = ["x_fwd", "y_fwd", "z", "y_inv", "x_inv", "update_p", "update_r", "other"]
+
+_lib = None
+
+
+def load():
+    """Load libgps.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError("libgps.so is not built; run paper_1509_00680_gb300.build.build()")
+        lib = ctypes.CDLL(LIB)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class GpsError(RuntimeError):
+    def __init__(self, status, where):
+        msg = load().gps_status_string(status).decode()
+        super().__init__("%s: %s (status %d)" % (where, msg, status))
+        self.status = status
+
+
+def _check(status, where, allow=(GPS_OK,)):
+    if status not in allow:
+        raise GpsError(status, where)
+    return status
+
+
+def make_grid(nx, ny, nz, hx, hy, hz, bc):
+    return gps_grid(int(nx), int(ny), int(nz), float(hx), float(hy), float(hz), int(bc))
+
+
+def grid_from(g):
+    """gps_grid from any object with nx..hz and bc attributes."""
+    return make_grid(g.nx, g.ny, g.nz, g.hx, g.hy, g.hz, g.bc)
+
+
+def make_electrolyte(z, c_molar, temperature=300.0, eps0=78.36):
+    el = gps_electrolyte()
+    el.nspecies = len(z)
+    for i, (zi, ci) in enumerate(zip(z, c_molar)):
+        el.z[i] = int(zi)
+        el.c_molar[i] = float(ci)
+    el.temperature = float(temperature)
+    el.eps0 = float(eps0)
+    return el
+
+
+def default_opts(**kw):
+    o = gps_opts()
+    load().gps_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _dev(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a):
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise TypeError("expected a C-contiguous float64 numpy array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Context:
+    """Owns one gps_ctx (plans, workspaces) on a CUDA device."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.gps_create(ctypes.byref(h), int(device), int(hbm_budget_bytes)), "gps_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().gps_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bytes_in_use(self):
+        return int(load().gps_bytes_in_use(self.handle))
+
+    def set_profiling(self, enabled):
+        _check(load().gps_set_profiling(self.handle, int(bool(enabled))), "gps_set_profiling")
+
+    def get_profile(self, reset=False):
+        """{kind: (launches, total_ms)} of the kernels timed since the last reset."""
+        n = (ctypes.c_longlong * GPS_PROFILE_KINDS)()
+        t = (ctypes.c_double * GPS_PROFILE_KINDS)()
+        _check(load().gps_get_profile(self.handle, n, t, int(bool(reset))), "gps_get_profile")
+        return {k: (int(n[i]), float(t[i])) for i, k in enumerate(PROFILE_KINDS)}
+
+    # --- device arrays -------------------------------------------------
+    def gpe_solve(self, grid, rho, eps, phi, opts=None, stream=None, allow=(GPS_OK,)):
+        rep = gps_report()
+        o = opts if opts is not None else default_opts()
+        s = load().gps_gpe_solve(self.handle, ctypes.byref(grid), _dev(rho), _dev(eps), _dev(phi),
+                                 ctypes.byref(o), ctypes.byref(rep), _stream(stream))
+        _check(s, "gps_gpe_solve", allow)
+        return rep
+
+    def pb_solve(self, grid, rho, eps, electrolyte, kind, phi, opts=None, stream=None, allow=(GPS_OK,)):
+        rep = gps_report()
+        o = opts if opts is not None else default_opts()
+        s = load().gps_pb_solve(self.handle, ctypes.byref(grid), _dev(rho), _dev(eps),
+                                ctypes.byref(electrolyte), int(KIND.get(kind, kind)), _dev(phi),
+                                ctypes.byref(o), ctypes.byref(rep), _stream(stream))
+        _check(s, "gps_pb_solve", allow)
+        return rep
+
+    # --- host arrays ---------------------------------------------------
+    def gpe_solve_host(self, grid, rho, eps, phi, opts=None, stream=None):
+        rep = gps_report()
+        o = opts if opts is not None else default_opts()
+        s = load().gps_gpe_solve_host(self.handle, ctypes.byref(grid), _host(rho), _host(eps),
+                                      _host(phi), ctypes.byref(o), ctypes.byref(rep), _stream(stream))
+        _check(s, "gps_gpe_solve_host")
+        return rep
+
+    def pb_solve_host(self, grid, rho, eps, electrolyte, kind, phi, opts=None, stream=None):
+        rep = gps_report()
+        o = opts if opts is not None else default_opts()
+        s = load().gps_pb_solve_host(self.handle, ctypes.byref(grid), _host(rho), _host(eps),
+                                     ctypes.byref(electrolyte), int(KIND.get(kind, kind)),
+                                     _host(phi), ctypes.byref(o), ctypes.byref(rep), _stream(stream))
+        _check(s, "gps_pb_solve_host")
+        return rep
+
+    # --- steps -----------------------------------------------------------
+    def setup_fields(self, grid, eps, s, q, stream=None):
+        _check(load().gps_setup_fields(self.handle, ctypes.byref(grid), _dev(eps), _dev(s), _dev(q),
+                                       _stream(stream)), "gps_setup_fields")
+
+    def vacuum_solve(self, grid, sigma, w, stream=None):
+        _check(load().gps_vacuum_solve(self.handle, ctypes.byref(grid), _dev(sigma), _dev(w),
+                                       _stream(stream)), "gps_vacuum_solve")
+
+    def precondition(self, grid, s, r, v, precision=GPS_FP64, stream=None):
+        _check(load().gps_precondition(self.handle, ctypes.byref(grid), _dev(s), _dev(r), _dev(v),
+                                       int(precision), _stream(stream)), "gps_precondition")
+
+    def ionic_charge(self, grid, phi, eps, electrolyte, out, stream=None):
+        _check(load().gps_ionic_charge(self.handle, ctypes.byref(grid), _dev(phi), _dev(eps),
+                                       ctypes.byref(electrolyte), _dev(out), _stream(stream)),
+               "gps_ionic_charge")
+
+
+def kernel_launches():
+    return int(load().gps_kernel_launches())
+
+
+# C-ABI names, for callers that prefer the flat interface.
+def gps_create(device=0, hbm_budget_bytes=0):
+    return Context(device, hbm_budget_bytes)
+
+
+def gps_destroy(ctx):
+    ctx.close()
+
+
+def gps_gpe_solve(ctx, grid, rho, eps, phi, opts=None, stream=None):
+    return ctx.gpe_solve(grid, rho, eps, phi, opts, stream)
+
+
+def gps_pb_solve(ctx, grid, rho, eps, electrolyte, kind, phi, opts=None, stream=None):
+    return ctx.pb_solve(grid, rho, eps, electrolyte, kind, phi, opts, stream)
+
+
+def gps_gpe_solve_host(ctx, grid, rho, eps, phi, opts=None, stream=None):
+    return ctx.gpe_solve_host(grid, rho, eps, phi, opts, stream)
+
+
+def gps_pb_solve_host(ctx, grid, rho, eps, electrolyte, kind, phi, opts=None, stream=None):
+    return ctx.pb_solve_host(grid, rho, eps, electrolyte, kind, phi, opts, stream)
+
+
+def gps_setup_fields(ctx, grid, eps, s, q, stream=None):
+    return ctx.setup_fields(grid, eps, s, q, stream)
+
+
+def gps_vacuum_solve(ctx, grid, sigma, w, stream=None):
+    return ctx.vacuum_solve(grid, sigma, w, stream)
+
+
+def gps_precondition(ctx, grid, s, r, v, precision=GPS_FP64, stream=None):
+    return ctx.precondition(grid, s, r, v, precision, stream)
+
+
+def gps_ionic_charge(ctx, grid, phi, eps, electrolyte, out, stream=None):
+    return ctx.ionic_charge(grid, phi, eps, electrolyte, out, stream)

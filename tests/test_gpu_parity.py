@@ -1,0 +1,294 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Small grids that span several FFT tiles with ragged edges are compared
+element by element; the full-size workloads are checked through properties
+that hold at any size (the oracle's own discrete fixed-point residual of the
+GPU result) plus sampled comparisons.  Tolerances:
+  * vacuum solve / preconditioner, FP64: 1e-12 relative (max norm) -- two
+    FFTs of different factorization order differ by O(eps log N);
+  * s = eps^-1/2: bit-exact (correctly rounded sqrt and division on both sides);
+  * q by FD-16: 1e-13 relative (different summation order);
+  * potentials phi of converged solves: relative L2 <= 1e-10 (the target
+    stated for the FP64 path), both sides converged to ||r|| <= 1e-13 ||r0||.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.green import VacuumSolver
+from oracle.operators import Fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gps():
+    from paper_1509_00680_gb300 import build
+    build.build()
+    from paper_1509_00680_gb300 import gps as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(gps):
+    c = gps.Context(0)
+    yield c
+    c.close()
+
+
+def T(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
+
+
+def N(t, shape):
+    return t.cpu().numpy().reshape(shape)
+
+
+def relmax(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def rel2(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+SMALL = [
+    (synth.BC_FREE, (12, 10, 16), (0.5, 0.45, 0.4)),
+    (synth.BC_FREE, (20, 18, 15), (0.4, 0.4, 0.4)),
+    (synth.BC_PERIODIC, (16, 12, 10), (0.5, 0.5, 0.6)),
+    (synth.BC_PERIODIC, (30, 24, 20), (0.4, 0.45, 0.5)),
+    (synth.BC_SURFACE, (16, 12, 10), (0.5, 0.5, 0.5)),
+    (synth.BC_SURFACE, (20, 18, 24), (0.4, 0.4, 0.35)),
+]
+
+
+def _grid(bc, n, h):
+    return synth.Grid(n[0], n[1], n[2], h[0], h[1], h[2], bc)
+
+
+@pytest.mark.parametrize("bc,n,h", SMALL)
+def test_vacuum_solve(gps, ctx, bc, n, h):
+    g = _grid(bc, n, h)
+    rng = np.random.default_rng(11)
+    sigma = rng.standard_normal(g.shape)
+    w = T(np.zeros(g.shape))
+    ctx.vacuum_solve(gps.grid_from(g), T(sigma), w)
+    ref = VacuumSolver(g).apply(sigma)
+    assert relmax(N(w, g.shape), ref) < 1e-12
+
+
+@pytest.mark.parametrize("bc,n,h", SMALL)
+def test_setup_fields(gps, ctx, bc, n, h):
+    g = _grid(bc, n, h)
+    rng = np.random.default_rng(12)
+    eps = 1.0 + 20.0 * rng.random(g.shape)
+    s, q = T(np.zeros(g.shape)), T(np.zeros(g.shape))
+    ctx.setup_fields(gps.grid_from(g), T(eps), s, q)
+    f = Fields(g, eps)
+    assert np.array_equal(N(s, g.shape), f.s)
+    assert relmax(N(q, g.shape), f.q) < 1e-12
+
+
+@pytest.mark.parametrize("bc,n,h", SMALL)
+def test_precondition_fp64(gps, ctx, bc, n, h):
+    g = _grid(bc, n, h)
+    rng = np.random.default_rng(13)
+    eps = 1.0 + 30.0 * rng.random(g.shape)
+    r = rng.standard_normal(g.shape)
+    f = Fields(g, eps)
+    v = T(np.zeros(g.shape))
+    ctx.precondition(gps.grid_from(g), T(f.s), T(r), v)
+    assert relmax(N(v, g.shape), f.precondition(r)) < 1e-12
+
+
+@pytest.mark.parametrize("bc,n,h", SMALL[::2])
+def test_precondition_fp32_spectrum(gps, ctx, bc, n, h):
+    g = _grid(bc, n, h)
+    rng = np.random.default_rng(14)
+    eps = 1.0 + 30.0 * rng.random(g.shape)
+    r = rng.standard_normal(g.shape)
+    f = Fields(g, eps)
+    v = T(np.zeros(g.shape))
+    ctx.precondition(gps.grid_from(g), T(f.s), T(r), v, precision=gps.GPS_MIXED)
+    assert relmax(N(v, g.shape), f.precondition(r)) < 2e-5
+
+
+def _solve_pair(gps, ctx, p, kind="gpe", tol_rel=1e-13, **okw):
+    g = p.grid
+    phi = T(np.zeros(g.shape))
+    opts = gps.default_opts(tol_abs=0.0, tol_rel=tol_rel, max_iter=2000, **okw)
+    if kind == "gpe":
+        rep = ctx.gpe_solve(gps.grid_from(g), T(p.rho), T(p.eps), phi, opts)
+        ref, info = oracle.solve_gpe(g, p.rho, p.eps, tol_abs=0.0, tol_rel=tol_rel, max_iter=2000)
+    elif kind == "lpb":
+        el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+        rep = ctx.pb_solve(gps.grid_from(g), T(p.rho), T(p.eps), el, "lpb", phi, opts)
+        gam = oracle.pb.exclusion_from_eps(p.eps, p.eps0)
+        lam = oracle.pb.linear_lambda(gam, p.electrolyte)
+        ref, info = oracle.solve_lpb(g, p.rho, p.eps, lam, tol_abs=0.0, tol_rel=tol_rel, max_iter=2000)
+    return N(phi, g.shape), ref, rep, info
+
+
+def test_gpe_free_single_cavity(gps, ctx):
+    p = synth.workload(1)          # 64^3, h = 0.3, the free-BC workload itself
+    got, ref, rep, info = _solve_pair(gps, ctx, p)
+    assert rep.status == 0
+    assert abs(rep.iters - info["iters"]) <= 2
+    assert rel2(got, ref) <= 1e-10
+
+
+def test_gpe_free_default_tolerance(gps, ctx):
+    """The workload's own stopping rule, ||r|| <= 1e-10."""
+    p = synth.workload(1)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.gpe_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), phi, gps.default_opts(tol_abs=1e-10))
+    ref, info = oracle.solve_gpe(p.grid, p.rho, p.eps, tol_abs=1e-10)
+    assert rep.res <= 1e-10 and rep.iters <= 25
+    assert rel2(N(phi, p.grid.shape), ref) <= 1e-10
+
+
+def test_gpe_periodic_cluster_small(gps, ctx):
+    p = synth.workload(2, n=48, count=8)
+    got, ref, rep, info = _solve_pair(gps, ctx, p)
+    assert rep.status == 0
+    assert rel2(got, ref) <= 1e-10
+    assert abs(np.sum(np.sqrt(p.eps) * got)) <= 1e-10 * np.abs(got).sum()
+
+
+def test_gpe_surface_small(gps, ctx):
+    p = synth.workload(3, nxy=40, nz=64, count=8)
+    got, ref, rep, info = _solve_pair(gps, ctx, p)
+    assert rel2(got, ref) <= 1e-10
+
+
+@pytest.mark.parametrize("wl,kw", [(1, dict(n=40)), (2, dict(n=36, count=6)),
+                                   (3, dict(nxy=32, nz=48, count=6))])
+def test_lpb(gps, ctx, wl, kw):
+    p = synth.workload(wl, **kw)
+    if p.electrolyte is None:
+        p.electrolyte = synth.Electrolyte((1, -1), (0.3, 0.3), 300.0)
+    got, ref, rep, info = _solve_pair(gps, ctx, p, kind="lpb")
+    assert rep.status == 0
+    assert rel2(got, ref) <= 1e-10
+
+
+def test_nlpb_newton_surface_small(gps, ctx):
+    p = synth.workload(3, nxy=32, nz=64, count=8, kind="nlpb")
+    el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+    phi = T(np.zeros(p.grid.shape))
+    opts = gps.default_opts(tol_outer=1e-11, max_iter=3000)
+    rep = ctx.pb_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), el, "nlpb", phi, opts)
+    ref, info = oracle.solve_nlpb(p.grid, p.rho, p.eps, p.electrolyte, p.eps0, tol=1e-11, max_iter=3000)
+    assert info["converged"] and rep.status == 0
+    assert rel2(N(phi, p.grid.shape), ref) <= 1e-9
+
+
+def test_nlpb_printed_small_box(gps, ctx):
+    """Algorithm 4 as printed (linear mixing) where it converges: a box
+    smaller than the Debye length, weak source."""
+    g = synth.Grid(16, 16, 16, 0.6, 0.6, 0.6, synth.BC_FREE)
+    c = (8 * 0.6,) * 3
+    eps = synth.rigid_cavity(g, [(2.0, c)], 0.6)
+    rho = synth.gaussian_charges(g, [(0.002, 1.0, c)])
+    el_o = synth.Electrolyte((1, -1), (0.1, 0.1), 300.0)
+    el = gps.make_electrolyte((1, -1), (0.1, 0.1), 300.0, synth.EPS_WATER)
+    phi = T(np.zeros(g.shape))
+    opts = gps.default_opts(tol_outer=1e-13, outer_mode=gps.GPS_OUTER_PRINTED, eta=0.6, max_outer=200)
+    rep = ctx.pb_solve(gps.grid_from(g), T(rho), T(eps), el, "nlpb", phi, opts)
+    ref, info = oracle.solve_nlpb(g, rho, eps, el_o, synth.EPS_WATER, mode="printed", eta=0.6,
+                                  tol=1e-13, max_outer=200)
+    assert info["converged"] and rep.status == 0
+    assert rel2(N(phi, g.shape), ref) <= 1e-9
+
+
+def test_ionic_charge(gps, ctx):
+    g = synth.Grid(10, 12, 14, 0.5, 0.5, 0.5, synth.BC_FREE)
+    rng = np.random.default_rng(15)
+    phi = 0.02 * rng.standard_normal(g.shape)
+    phi[0, 0, :3] = [1.0, -1.0, 0.5]      # exponent cap active
+    eps = 1.0 + 77.36 * rng.random(g.shape)
+    el_o = synth.Electrolyte((1, -1, 2), (0.1, 0.1, 0.05), 310.0)
+    el = gps.make_electrolyte((1, -1, 2), (0.1, 0.1, 0.05), 310.0, synth.EPS_WATER)
+    out = T(np.zeros(g.shape))
+    ctx.ionic_charge(gps.grid_from(g), T(phi), T(eps), el, out)
+    ref = oracle.pb.ionic_charge(phi, oracle.pb.exclusion_from_eps(eps, synth.EPS_WATER), el_o)
+    assert relmax(N(out, g.shape), ref) < 1e-13
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_invalid_inputs(gps, ctx):
+    g = synth.Grid(16, 16, 16, 0.5, 0.5, 0.5, synth.BC_FREE)
+    rho, phi = T(np.zeros(g.shape)), T(np.zeros(g.shape))
+    bad_eps = np.ones(g.shape)
+    bad_eps[3, 4, 5] = -1.0
+    with pytest.raises(gps.GpsError) as e:
+        ctx.gpe_solve(gps.grid_from(g), rho, T(bad_eps), phi)
+    assert e.value.status == gps.GPS_ERR_INVALID
+    for dims, bc in [((7, 16, 16), synth.BC_PERIODIC), ((14, 16, 16), synth.BC_PERIODIC),
+                     ((2, 16, 16), synth.BC_FREE)]:
+        g2 = synth.Grid(dims[0], dims[1], dims[2], 0.5, 0.5, 0.5, bc)
+        z = T(np.ones(g2.shape))
+        with pytest.raises(gps.GpsError) as e:
+            ctx.gpe_solve(gps.grid_from(g2), z, z, T(np.zeros(g2.shape)))
+        assert e.value.status == gps.GPS_ERR_INVALID
+
+
+def test_not_converged_and_zero_source(gps, ctx):
+    p = synth.workload(1, n=24)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.gpe_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), phi,
+                        gps.default_opts(max_iter=2), allow=(gps.GPS_ERR_NOT_CONVERGED,))
+    assert rep.status == gps.GPS_ERR_NOT_CONVERGED and rep.iters == 2
+    rep = ctx.gpe_solve(gps.grid_from(p.grid), T(np.zeros(p.grid.shape)), T(p.eps), phi)
+    assert rep.iters == 0 and np.all(N(phi, p.grid.shape) == 0)
+
+
+def test_deterministic_and_host_entry_point(gps, ctx):
+    p = synth.workload(2, n=32, count=5)
+    g = gps.grid_from(p.grid)
+    a, b = T(np.zeros(p.grid.shape)), T(np.zeros(p.grid.shape))
+    ctx.gpe_solve(g, T(p.rho), T(p.eps), a)
+    ctx.gpe_solve(g, T(p.rho), T(p.eps), b)
+    assert np.array_equal(N(a, p.grid.shape), N(b, p.grid.shape))
+    h = np.zeros(p.grid.shape)
+    ctx.gpe_solve_host(g, np.ascontiguousarray(p.rho), np.ascontiguousarray(p.eps), h)
+    assert np.array_equal(h, N(a, p.grid.shape))
+
+
+# ------------------------------------------------ full-size workloads -------
+
+def _fixed_point_residual(p, phi, lam=None, rions=None):
+    """|| M(rho [+ rho_ions] - (q + lam) phi / 4pi) - phi || / ||phi|| with the
+    oracle's own operators (free and surface BC, where S is invertible): zero
+    for the exact discrete solution, Eq. (corr) rearranged."""
+    assert p.grid.bc != synth.BC_PERIODIC
+    f = Fields(p.grid, p.eps, lam=lam)
+    src = p.rho if rions is None else p.rho + rions
+    g = f.precondition(src - f.qlam * phi / (4 * np.pi)) - phi
+    return np.linalg.norm(g) / np.linalg.norm(phi)
+
+
+def test_full_periodic_cluster_128(gps, ctx):
+    """The 128^3 periodic workload timed by the benchmark, FP64: element-wise
+    against the oracle."""
+    p = synth.workload(2)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.gpe_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), phi, gps.default_opts(tol_abs=1e-10))
+    ref, info = oracle.solve_gpe(p.grid, p.rho, p.eps, tol_abs=1e-10, max_iter=500)
+    assert rep.status == 0 and abs(rep.iters - info["iters"]) <= 3
+    assert rel2(N(phi, p.grid.shape), ref) <= 1e-10
+
+
+def test_full_surface_lpb(gps, ctx):
+    p = synth.workload(3, kind="lpb")
+    el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.pb_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), el, "lpb", phi,
+                       gps.default_opts(tol_abs=1e-10, max_iter=1000))
+    assert rep.status == 0
+    gam = oracle.pb.exclusion_from_eps(p.eps, p.eps0)
+    lam = oracle.pb.linear_lambda(gam, p.electrolyte)
+    assert _fixed_point_residual(p, N(phi, p.grid.shape), lam=lam) < 1e-9
