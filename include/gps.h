@@ -182,15 +182,18 @@ int gps_ionic_charge(gps_ctx* ctx, const gps_grid* grid, const double* phi_dev,
                      const double* eps_dev, const gps_electrolyte* el,
                      double* out_dev, void* cuda_stream);
 
-/* Instrumentation.  With profiling on, every kernel that the solve entry
- * points launch is bracketed by CUDA events on the call's stream; the
- * elapsed times are collected when the call returns.  Kernel kinds:
- * 0 x_fwd, 1 y_fwd, 2 z (forward, Green's multiply, inverse), 3 y_inv,
- * 4 x_inv, 5 update_p, 6 update_r, 7 setup and other.
- * gps_get_profile writes per kind the launch count and total milliseconds
- * accumulated since the last reset (arrays of GPS_PROFILE_KINDS entries). */
+/* Instrumentation.  gps_set_profiling(ctx, mask): every kernel of a kind
+ * whose bit is set in `mask` that the solve entry points launch is
+ * bracketed by CUDA events on the call's stream, and the elapsed times are
+ * collected when the call returns (mask 0 turns profiling off, 0xFF times
+ * every kind).  Kernel kinds: 0 x_fwd, 1 y_fwd, 2 z (forward, Green's
+ * multiply, inverse), 3 y_inv, 4 x_inv, 5 update_p, 6 update_r, 7 setup.
+ * Launches that return at once because the PCG had already converged are
+ * not counted.  gps_get_profile writes per kind the launch count and the
+ * total milliseconds accumulated since the last reset (arrays of
+ * GPS_PROFILE_KINDS entries). */
 #define GPS_PROFILE_KINDS 8
-int gps_set_profiling(gps_ctx* ctx, int enabled);
+int gps_set_profiling(gps_ctx* ctx, int mask);
 int gps_get_profile(gps_ctx* ctx, long long* launches, double* total_ms, int reset);
 
 /* Number of CUDA kernels this library has launched in the process so far. */

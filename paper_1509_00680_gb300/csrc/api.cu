@@ -135,6 +135,7 @@ struct Plan {
 // Opt-in per-kernel timing with CUDA events on the launching stream.
 struct Profiler {
   bool on = false;
+  int mask = 0;
   struct Rec { int kind; cudaEvent_t a, b; };
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
@@ -190,7 +191,7 @@ static thread_local Profiler* t_prof = nullptr;
 
 template <typename F>
 static void timed(int kind, cudaStream_t st, F&& f) {
-  if (!t_prof || !t_prof->on) {
+  if (!t_prof || !t_prof->on || !(t_prof->mask & (1 << kind))) {
     f();
     return;
   }
@@ -930,9 +931,10 @@ int gps_ionic_charge(gps_ctx* ctx, const gps_grid* grid, const double* phi, cons
   GPS_GUARD_END
 }
 
-int gps_set_profiling(gps_ctx* ctx, int enabled) {
+int gps_set_profiling(gps_ctx* ctx, int mask) {
   if (!ctx) return GPS_ERR_INVALID;
-  ctx->prof.on = enabled != 0;
+  ctx->prof.on = mask != 0;
+  ctx->prof.mask = mask;
   return GPS_OK;
 }
 

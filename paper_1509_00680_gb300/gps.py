@@ -185,8 +185,16 @@ class Context:
     def bytes_in_use(self):
         return int(load().gps_bytes_in_use(self.handle))
 
-    def set_profiling(self, enabled):
-        _check(load().gps_set_profiling(self.handle, int(bool(enabled))), "gps_set_profiling")
+    def set_profiling(self, kinds=None):
+        """Time the kernels of the given kinds (names of PROFILE_KINDS); None or
+        an empty list turns profiling off, "all" times every kind."""
+        if kinds == "all":
+            mask = (1 << GPS_PROFILE_KINDS) - 1
+        else:
+            mask = 0
+            for k in (kinds or []):
+                mask |= 1 << PROFILE_KINDS.index(k)
+        _check(load().gps_set_profiling(self.handle, mask), "gps_set_profiling")
 
     def get_profile(self, reset=False):
         """{kind: (launches, total_ms)} of the kernels timed since the last reset."""
