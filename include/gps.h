@@ -93,6 +93,7 @@ typedef struct {
   double forcing;        /* NLPB Newton: relative inner tolerance cap (e.g. 1e-2) */
   int precision;         /* gps_precision */
   double mixed_switch;   /* GPS_MIXED: FP64 preconditioner until ||r|| <= mixed_switch*||r_0|| */
+  int certify;           /* 1: compute rep->fixed_point_res (always done for GPS_MIXED) */
 } gps_opts;
 
 typedef struct {
@@ -104,6 +105,10 @@ typedef struct {
   double res;            /* ||r||_2 at exit of the (last) PCG */
   double outer_res;      /* NLPB: final ionic-charge residual */
   double background;     /* periodic GPe: mean of rho removed to neutralize the cell */
+  double fixed_point_res; /* ||g|| / ||phi||, g = M(rho [+ rho_ions] - (q + lambda) phi / 4pi)
+                             [+ <sqrt(eps) phi> s, periodic] - phi with an FP64 vacuum solve:
+                             zero for the exact discrete solution (certificate of the result);
+                             -1 when not computed */
   double time_ms;        /* wall time of the call (host clock, synchronized) */
 } gps_report;
 
@@ -111,7 +116,7 @@ typedef struct gps_ctx gps_ctx;
 
 /* Fill *opts with defaults: tol_abs 1e-10, tol_rel 0, max_iter 500,
  * max_outer 100, tol_outer 1e-10, eta 0.6, Newton outer mode, forcing 1e-2,
- * FP64, mixed_switch 1e-2. */
+ * FP64, mixed_switch 1e-3, certify 0. */
 void gps_default_opts(gps_opts* opts);
 
 /* Human-readable name of a status code (static storage). */

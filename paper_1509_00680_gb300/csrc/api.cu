@@ -111,6 +111,7 @@ struct Plan {
          *src = nullptr;
   double *io_rho = nullptr, *io_eps = nullptr, *io_phi = nullptr;
   double* partials = nullptr;
+  double* partials2 = nullptr;
   PcgScalars* sc = nullptr;
   PcgScalars* sc_host = nullptr;
   std::vector<void*> allocs;
@@ -384,6 +385,7 @@ Plan* build_plan(const gps_grid* gr, cudaStream_t st) {
   const size_t xb = ((g.nrows + 1) / 2 + g.lines_x - 1) / g.lines_x;
   if (xb > maxblocks) maxblocks = xb;
   P->partials = P->alloc<double>(maxblocks);
+  P->partials2 = P->alloc<double>(maxblocks);
   P->sc = P->alloc<PcgScalars>(1);
   ck(cudaMemsetAsync(P->sc, 0, sizeof(PcgScalars), st));
   ck(cudaMallocHost((void**)&P->sc_host, sizeof(PcgScalars)));
@@ -555,6 +557,22 @@ PcgResult run_pcg(Plan* P, const double* rho, double* phi, const double* qlam, d
   return res;
 }
 
+// Certificate of a result (FP64): ||g|| / ||phi|| with
+// g = M(rho - bg [+ rions] - qlam phi / 4pi) [+ <sqrt(eps) phi> s] - phi.
+// Uses P->p and P->Ap as scratch.
+double certify(Plan* P, const double* rho, double bg, const double* rions, const double* qlam,
+               const double* phi, double k0, int use_k0, cudaStream_t st) {
+  const bool periodic = P->bc == GPS_BC_PERIODIC;
+  launch_fp_source(rho, rions, qlam, phi, P->sq, P->p, P->n, bg, P->partials, P->sc, st);
+  vacuum_pipeline<double2>(P, P->p, P->s, P->table, k0, use_k0, P->Ap, P->s, nullptr, false, st);
+  read_scalars(P, st);
+  const double c = periodic ? P->sc_host->aux[5] / (double)P->n : 0.0;
+  launch_fp_residual(P->Ap, P->s, phi, P->n, c, P->partials, P->partials2, P->sc, st);
+  read_scalars(P, st);
+  const double nphi = std::sqrt(P->sc_host->aux[7]);
+  return nphi > 0 ? std::sqrt(P->sc_host->aux[6]) / nphi : std::sqrt(P->sc_host->aux[6]);
+}
+
 IonParams ion_params(const gps_electrolyte* el) {
   const double NA = 6.02214076e23, a0 = 5.29177210903e-11, kB = 3.1668115634556e-6;
   IonParams ip;
@@ -601,6 +619,7 @@ void fill_report(gps_report* rep, const PcgResult& r, double t0) {
   rep->res0 = r.res0;
   rep->res = r.res;
   rep->background = r.background;
+  rep->fixed_point_res = -1.0;
   rep->time_ms = now_ms() - t0;
 }
 
@@ -625,9 +644,12 @@ int solve_core(gps_ctx* ctx, const gps_grid* gr, const double* rho, const double
   const bool periodic = P->bc == GPS_BC_PERIODIC;
   const double N = (double)P->n;
   const double invN = 1.0 / ((double)P->Px * P->Py * P->Pz);
+  const bool want_cert = o.certify || o.precision == GPS_MIXED;
   if (kind == GPS_GPE) {
     PcgResult r = run_pcg(P, rho, phi, P->q, 0.0, 0, periodic, &o, st);
     fill_report(rep, r, t0);
+    if (rep && want_cert && r.status == GPS_OK)
+      rep->fixed_point_res = certify(P, rho, r.background, nullptr, P->q, phi, 0.0, 0, st);
     return r.status;
   }
   const double lam0 = lambda0_of(el);
@@ -643,9 +665,11 @@ int solve_core(gps_ctx* ctx, const gps_grid* gr, const double* rho, const double
     read_scalars(P, st);
     const double lam_mean = P->sc_host->aux[1] / N;
     const bool k0 = periodic && lam_mean > 0;
-    PcgResult r = run_pcg(P, rho, phi, P->qlam, k0 ? kFourPi * eps_mean / lam_mean * invN : 0.0,
-                          k0 ? 1 : 0, periodic && !k0, &o, st);
+    const double k0v = k0 ? kFourPi * eps_mean / lam_mean * invN : 0.0;
+    PcgResult r = run_pcg(P, rho, phi, P->qlam, k0v, k0 ? 1 : 0, periodic && !k0, &o, st);
     fill_report(rep, r, t0);
+    if (rep && want_cert && r.status == GPS_OK)
+      rep->fixed_point_res = certify(P, rho, r.background, nullptr, P->qlam, phi, k0v, k0 ? 1 : 0, st);
     return r.status;
   }
   if (kind != GPS_NLPB) return GPS_ERR_INVALID;
@@ -706,8 +730,14 @@ int solve_core(gps_ctx* ctx, const gps_grid* gr, const double* rho, const double
     launch_nl_step(phi, eps, P->rions, P->rp, P->fresh, P->lam, P->dphi, P->r, P->n, ip, e, t, 1,
                    P->partials, P->sc, st);
   }
+  double cert = -1.0;
+  if (want_cert && status == GPS_OK) {
+    launch_ionic_charge(phi, eps, P->fresh, P->n, ip, st);
+    cert = certify(P, rho, 0.0, P->fresh, P->q, phi, 0.0, 0, st);
+  }
   ck(cudaStreamSynchronize(st));
   if (rep) {
+    rep->fixed_point_res = cert;
     rep->status = status;
     rep->iters = total_iters;
     rep->fp64_iters = fp64_iters;
@@ -737,7 +767,8 @@ void gps_default_opts(gps_opts* o) {
   o->outer_mode = GPS_OUTER_NEWTON;
   o->forcing = 1e-2;
   o->precision = GPS_FP64;
-  o->mixed_switch = 1e-2;
+  o->mixed_switch = 1e-3;
+  o->certify = 0;
 }
 
 const char* gps_status_string(int s) {

@@ -204,6 +204,38 @@ __global__ void k_update_r(double* __restrict__ phi, double* __restrict__ r,
   }
 }
 
+// ----------------------------------------------------------- certificate --
+
+// out = rho - bg [+ rions] - qlam phi / 4 pi ; partial of sqrt(eps) phi.
+__global__ void k_fp_source(const double* __restrict__ rho, const double* __restrict__ rions,
+                            const double* __restrict__ qlam, const double* __restrict__ phi,
+                            const double* __restrict__ sq, double* __restrict__ out, size_t n,
+                            double bg, double* partials, PcgScalars* sc) {
+  double acc = 0.0;
+  const double inv4pi = 1.0 / kFourPi;
+  GRID_STRIDE(i, n) {
+    double src = rho[i] - bg - qlam[i] * phi[i] * inv4pi;
+    if (rions) src += rions[i];
+    out[i] = src;
+    acc += sq[i] * phi[i];
+  }
+  grid_reduce(acc, partials, &sc->counter[CNT_AUX], &sc->aux[5]);
+}
+
+// g = w + c s - phi ; partials of ||g||^2 (aux[6]) and ||phi||^2 (aux[7]).
+__global__ void k_fp_residual(const double* __restrict__ w, const double* __restrict__ s,
+                              const double* __restrict__ phi, size_t n, double c, double* partials,
+                              double* partials2, PcgScalars* sc) {
+  double a = 0.0, b = 0.0;
+  GRID_STRIDE(i, n) {
+    const double g = w[i] + c * s[i] - phi[i];
+    a += g * g;
+    b += phi[i] * phi[i];
+  }
+  grid_reduce(a, partials, &sc->counter[CNT_AUX], &sc->aux[6]);
+  grid_reduce(b, partials2, &sc->counter[CNT_AUX2], &sc->aux[7]);
+}
+
 // ------------------------------------------------------------------ ions ---
 
 __device__ __forceinline__ void ion_terms(double phi, double gamma, const IonParams& ip,
@@ -433,6 +465,19 @@ void launch_update_r(double* phi, double* r, const double* p, const double* Ap, 
                      double* partials, PcgScalars* sc, cudaStream_t st) {
   count_launch();
   k_update_r<<<grid_blocks(n, kT), kT, 0, st>>>(phi, r, p, Ap, n, partials, sc);
+}
+
+void launch_fp_source(const double* rho, const double* rions, const double* qlam, const double* phi,
+                      const double* sq, double* out, size_t n, double bg, double* partials,
+                      PcgScalars* sc, cudaStream_t st) {
+  count_launch();
+  k_fp_source<<<grid_blocks(n, kT), kT, 0, st>>>(rho, rions, qlam, phi, sq, out, n, bg, partials, sc);
+}
+
+void launch_fp_residual(const double* w, const double* s, const double* phi, size_t n, double c,
+                        double* partials, double* partials2, PcgScalars* sc, cudaStream_t st) {
+  count_launch();
+  k_fp_residual<<<grid_blocks(n, kT), kT, 0, st>>>(w, s, phi, n, c, partials, partials2, sc);
 }
 
 void launch_ionic_charge(const double* phi, const double* eps, double* out, size_t n,

@@ -31,6 +31,11 @@ void launch_update_p(const double* v, const double* r, const double* qlam, const
                      PcgScalars* sc, cudaStream_t st);
 void launch_update_r(double* phi, double* r, const double* p, const double* Ap, size_t n,
                      double* partials, PcgScalars* sc, cudaStream_t st);
+void launch_fp_source(const double* rho, const double* rions, const double* qlam, const double* phi,
+                      const double* sq, double* out, size_t n, double bg, double* partials,
+                      PcgScalars* sc, cudaStream_t st);
+void launch_fp_residual(const double* w, const double* s, const double* phi, size_t n, double c,
+                        double* partials, double* partials2, PcgScalars* sc, cudaStream_t st);
 void launch_ionic_charge(const double* phi, const double* eps, double* out, size_t n,
                          const IonParams& ip, cudaStream_t st);
 void launch_nl_eval(const double* phi, const double* eps, const double* rions, const double* rp,

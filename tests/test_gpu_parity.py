@@ -292,3 +292,56 @@ def test_full_surface_lpb(gps, ctx):
     gam = oracle.pb.exclusion_from_eps(p.eps, p.eps0)
     lam = oracle.pb.linear_lambda(gam, p.electrolyte)
     assert _fixed_point_residual(p, N(phi, p.grid.shape), lam=lam) < 1e-9
+
+
+# ------------------------------------------------------ mixed precision -----
+
+@pytest.mark.parametrize("wl,kw,kind", [
+    (4, dict(n=64, count=12, margin=6.0, kind="gpe"), "gpe"),
+    (2, dict(n=48, count=8), "gpe"),
+    (3, dict(nxy=32, nz=48, count=6), "lpb"),
+])
+def test_mixed_precision_error(gps, ctx, wl, kw, kind):
+    """FP32 spectrum inside the FP64 PCG: relative L2 error against the FP64
+    oracle <= 1e-8, with the FP64 certificate of each result below 1e-8."""
+    p = synth.workload(wl, **kw)
+    g = p.grid
+    phi = T(np.zeros(g.shape))
+    opts = gps.default_opts(tol_abs=1e-10, precision=gps.GPS_MIXED, max_iter=2000)
+    if kind == "gpe":
+        rep = ctx.gpe_solve(gps.grid_from(g), T(p.rho), T(p.eps), phi, opts)
+        ref, _ = oracle.solve_gpe(g, p.rho, p.eps, tol_abs=0.0, tol_rel=1e-13, max_iter=2000)
+    else:
+        el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+        rep = ctx.pb_solve(gps.grid_from(g), T(p.rho), T(p.eps), el, "lpb", phi, opts)
+        lam = oracle.pb.linear_lambda(oracle.pb.exclusion_from_eps(p.eps, p.eps0), p.electrolyte)
+        ref, _ = oracle.solve_lpb(g, p.rho, p.eps, lam, tol_abs=0.0, tol_rel=1e-13, max_iter=2000)
+    err = rel2(N(phi, g.shape), ref)
+    assert rep.status == 0
+    assert 0 < rep.fp64_iters < rep.iters
+    assert 0 <= rep.fixed_point_res < 1e-8
+    assert err <= 1e-8
+
+
+def test_mixed_precision_nlpb(gps, ctx):
+    p = synth.workload(4, n=48, count=6, margin=5.0, kind="nlpb", conc=0.5)
+    el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+    phi = T(np.zeros(p.grid.shape))
+    opts = gps.default_opts(tol_outer=1e-10, precision=gps.GPS_MIXED, max_iter=3000)
+    rep = ctx.pb_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), el, "nlpb", phi, opts)
+    ref, info = oracle.solve_nlpb(p.grid, p.rho, p.eps, p.electrolyte, p.eps0, tol=1e-11, max_iter=3000)
+    assert rep.status == 0 and info["converged"]
+    assert 0 <= rep.fixed_point_res < 1e-8
+    assert rel2(N(phi, p.grid.shape), ref) <= 1e-8
+
+
+def test_fp64_certificate(gps, ctx):
+    p = synth.workload(1, n=40)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.gpe_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), phi,
+                        gps.default_opts(tol_abs=0.0, tol_rel=1e-13, certify=1))
+    assert 0 <= rep.fixed_point_res < 1e-12
+    p2 = synth.workload(2, n=32, count=5)
+    rep = ctx.gpe_solve(gps.grid_from(p2.grid), T(p2.rho), T(p2.eps), T(np.zeros(p2.grid.shape)),
+                        gps.default_opts(tol_abs=0.0, tol_rel=1e-13, certify=1))
+    assert 0 <= rep.fixed_point_res < 1e-12
