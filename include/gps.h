@@ -187,6 +187,31 @@ int gps_ionic_charge(gps_ctx* ctx, const gps_grid* grid, const double* phi_dev,
                      const double* eps_dev, const gps_electrolyte* el,
                      double* out_dev, void* cuda_stream);
 
+/* Vacuum Poisson solve w = S(sigma) (as gps_vacuum_solve) for callers that
+ * cannot allocate device memory -- for example a plugin whose host
+ * application owns the device-memory budget, a process whose framework has
+ * already reserved nearly all of HBM in its own pool, or a latency-critical
+ * loop that cannot afford the implicit device synchronization of
+ * cudaMalloc/cudaFree.  The paper has no counterpart: it is an interface
+ * variant of the vacuum solve.  No context is needed and no device memory
+ * is allocated: the twiddle tables, the Green's-function table and the
+ * spectrum live in one file-scope device array of 8 MiB that every GPU
+ * loading this library holds until the process exits.
+ * Supported: GPS_BC_PERIODIC and GPS_BC_SURFACE grids whose padded FFT
+ * lengths are even and factor into 2, 3 and 5, and whose spectrum
+ * ((nx/2+1)*ny*nz complex doubles) plus twiddle and octant tables fit in the
+ * 8 MiB array -- e.g. periodic grids up to 96^3.  Anything else returns
+ * GPS_ERR_INVALID.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call uses the same array and keeps the previous call's
+ * contents: calls that overlap on the GPU (other streams, other host
+ * threads) race with each other and must be serialized by the caller.
+ * sigma_dev, w_dev: nx*ny*nz doubles on the current device.  The call
+ * returns after synchronizing the stream. */
+int gps_vacuum_solve_noalloc(const gps_grid* grid, const double* sigma_dev, double* w_dev,
+                             void* cuda_stream);
+
 /* Instrumentation.  gps_set_profiling(ctx, mask): every kernel of a kind
  * whose bit is set in `mask` that the solve entry points launch is
  * bracketed by CUDA events on the call's stream, and the elapsed times are

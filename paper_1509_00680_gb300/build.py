@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgps.so")
-SOURCES = ["fft.cu", "kernels.cu", "api.cu"]
+SOURCES = ["fft.cu", "kernels.cu", "api.cu", "noalloc.cu"]
 HEADERS = ["gps_internal.h", "device_util.cuh", "kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -76,6 +76,7 @@ _SIGS = {
     "gps_precondition": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P, ctypes.c_int, _P]),
     "gps_ionic_charge": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P,
                                         ctypes.POINTER(gps_electrolyte), _P, _P]),
+    "gps_vacuum_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(gps_grid), _P, _P, _P]),
     "gps_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "gps_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
@@ -257,6 +258,17 @@ class Context:
         _check(load().gps_ionic_charge(self.handle, ctypes.byref(grid), _dev(phi), _dev(eps),
                                        ctypes.byref(electrolyte), _dev(out), _stream(stream)),
                "gps_ionic_charge")
+
+
+def vacuum_solve_noalloc(grid, sigma, w, stream=None):
+    """w = S(sigma) without any device allocation (periodic / surface BC,
+    sizes bounded by the library's fixed 8 MiB scratch array).  Calls that
+    overlap on the GPU share that array and race; serialize them."""
+    _check(load().gps_vacuum_solve_noalloc(ctypes.byref(grid), _dev(sigma), _dev(w), _stream(stream)),
+           "gps_vacuum_solve_noalloc")
+
+
+gps_vacuum_solve_noalloc = vacuum_solve_noalloc
 
 
 def kernel_launches():
