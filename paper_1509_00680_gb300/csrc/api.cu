@@ -460,7 +460,7 @@ int get_plan(gps_ctx* c, const gps_grid* gr, cudaStream_t st, Plan** out) {
 template <typename V>
 void vacuum_pipeline(Plan* P, const double* in, const double* in_scale, const double* table,
                      double k0, int use_k0, double* out, const double* out_scale,
-                     const double* dot_with, bool track, cudaStream_t st) {
+                     const double* dot_with, bool track, cudaStream_t st, bool gauge = false) {
   V* W;
   const V *twx, *twy, *twz;
   if constexpr (sizeof(V) == sizeof(double2)) {
@@ -476,15 +476,18 @@ void vacuum_pipeline(Plan* P, const double* in, const double* in_scale, const do
   }
   const PassGeom& g = P->g64;
   const int* done = track ? &P->sc->done : nullptr;
-  timed(0, st, [&] { launch_x_fwd<V>(g, P->fx.sched, twx, in, in_scale, W, done, st); });
-  timed(1, st, [&] { launch_y<V>(g, P->fy.sched, twy, W, false, done, st); });
-  timed(2, st, [&] {
-    launch_z<V>(g, P->fz.sched, twz, W, table, k0, use_k0, track ? &P->sc->mu_sum : nullptr, done, st);
+  const bool periodic_track = track && P->bc == GPS_BC_PERIODIC;
+  timed(0, st, [&] {
+    launch_x_fwd<V>(g, P->fx.sched, twx, in, in_scale, W, done, st, P->partials, P->sc,
+                    periodic_track ? &P->sc->mu_sum : nullptr);
   });
+  timed(1, st, [&] { launch_y<V>(g, P->fy.sched, twy, W, false, done, st); });
+  timed(2, st, [&] { launch_z<V>(g, P->fz.sched, twz, W, table, k0, use_k0, nullptr, done, st); });
   timed(3, st, [&] { launch_y<V>(g, P->fy.sched, twy, W, true, done, st); });
   timed(4, st, [&] {
     launch_x_inv<V>(g, P->fx.sched, twx, W, out, out_scale, dot_with, dot_with ? P->partials : nullptr,
-                    P->sc, CNT_VR, &P->sc->vr, done, st);
+                    P->sc, CNT_VR, &P->sc->vr, done, st, P->partials2,
+                    gauge ? &P->sc->wsum : nullptr);
   });
 }
 
@@ -531,16 +534,18 @@ PcgResult run_pcg(Plan* P, const double* rho, double* phi, const double* qlam, d
                 P->sc_host->background};
   const bool mixed = o->precision == GPS_MIXED;
   if (mixed) ensure_w32(P);
+  const bool gauge = periodic && !use_k0;   // singular periodic operator: keep v on the gauge
   bool use32 = false;
   int chunk = 2;
   while (!P->sc_host->done) {
     for (int c = 0; c < chunk; ++c) {
       if (use32)
-        vacuum_pipeline<float2>(P, P->r, P->s, P->table, k0, use_k0, P->v, P->s, P->r, true, st);
+        vacuum_pipeline<float2>(P, P->r, P->s, P->table, k0, use_k0, P->v, P->s, P->r, true, st, gauge);
       else
-        vacuum_pipeline<double2>(P, P->r, P->s, P->table, k0, use_k0, P->v, P->s, P->r, true, st);
+        vacuum_pipeline<double2>(P, P->r, P->s, P->table, k0, use_k0, P->v, P->s, P->r, true, st, gauge);
       timed(5, st, [&] {
-        launch_update_p(P->v, P->r, qlam, P->sq, P->p, P->Ap, P->n, periodic ? 1 : 0, P->partials, sc, st);
+        launch_update_p(P->v, P->r, qlam, P->sq, P->s, P->p, P->Ap, P->n, periodic ? 1 : 0,
+                        gauge ? 1 : 0, P->partials, sc, st);
       });
       timed(6, st, [&] { launch_update_r(phi, P->r, P->p, P->Ap, P->n, P->partials, sc, st); });
     }
@@ -767,7 +772,7 @@ void gps_default_opts(gps_opts* o) {
   o->outer_mode = GPS_OUTER_NEWTON;
   o->forcing = 1e-2;
   o->precision = GPS_FP64;
-  o->mixed_switch = 1e-3;
+  o->mixed_switch = 1e-2;
   o->certify = 0;
 }
 

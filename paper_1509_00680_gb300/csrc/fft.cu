@@ -176,7 +176,9 @@ template <typename V>
 __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, const V* __restrict__ twg,
                                                    const double* __restrict__ in,
                                                    const double* __restrict__ scale,
-                                                   V* __restrict__ W, const int* __restrict__ done) {
+                                                   V* __restrict__ W, const int* __restrict__ done,
+                                                   double* __restrict__ partials, PcgScalars* sc,
+                                                   double* sum_out) {
   using T = typename Real<V>::T;
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -188,6 +190,7 @@ __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, cons
   const int npairs = (g.nrows + 1) >> 1;
   const int p0 = blockIdx.x * g.lines_x;
   const int nl = min(g.lines_x, npairs - p0);
+  double sum = 0.0;
   for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
     const int l = idx / L, j = idx - l * L;
     const int ra = 2 * (p0 + l);
@@ -201,6 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, cons
         if (scale) b *= scale[oa + g.nx];
       }
     }
+    sum += a + b;
     b0[l * ls + j] = mk<V>((T)a, (T)b);
   }
   __syncthreads();
@@ -214,6 +218,7 @@ __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, cons
     W[row_offset(g, ra) + k] = mk<V>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
     if (ra + 1 < g.nrows) W[row_offset(g, ra + 1) + k] = mk<V>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
   }
+  if (sum_out) grid_reduce(sum, partials, &sc->counter[CNT_MU], sum_out);
 }
 
 template <typename V, int DIR>
@@ -303,7 +308,8 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
                                                    const double* __restrict__ dot_with,
                                                    double* __restrict__ partials, PcgScalars* sc,
                                                    int slot, double* dot_out,
-                                                   const int* __restrict__ done) {
+                                                   const int* __restrict__ done,
+                                                   double* __restrict__ partials2, double* wsum_out) {
   using T = typename Real<V>::T;
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -333,12 +339,13 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
   }
   __syncthreads();
   const V* res = fft_lines<V, +1>(b0, b1, s, ls, nl, tw);
-  double dot = 0.0;
+  double dot = 0.0, wsum = 0.0;
   for (int idx = threadIdx.x; idx < nl * g.nx; idx += blockDim.x) {
     const int l = idx / g.nx, j = idx - l * g.nx;
     const int ra = 2 * (p0 + l);
     const V zz = res[l * ls + j];
     const size_t oa = (size_t)ra * g.nx + j;
+    wsum += (double)zz.x + ((ra + 1 < g.nrows) ? (double)zz.y : 0.0);
     double va = (double)zz.x;
     if (out_scale) va *= out_scale[oa];
     out[oa] = va;
@@ -352,6 +359,7 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
     }
   }
   if (partials) grid_reduce(dot, partials, &sc->counter[slot], dot_out);
+  if (wsum_out) grid_reduce(wsum, partials2, &sc->counter[CNT_WSUM], wsum_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -368,13 +376,14 @@ static void set_smem(K kernel, size_t bytes) {
 
 template <typename V>
 void launch_x_fwd(const PassGeom& g, const FftSched& s, const V* tw, const double* in,
-                  const double* scale, V* W, const int* done, cudaStream_t st) {
+                  const double* scale, V* W, const int* done, cudaStream_t st, double* partials,
+                  PcgScalars* sc, double* sum_out) {
   const int npairs = (g.nrows + 1) / 2;
   const int blocks = (npairs + g.lines_x - 1) / g.lines_x;
   const size_t sm = x_lines_smem_bytes(s.L, g.lines_x, sizeof(V));
   set_smem(k_x_fwd<V>, sm);
   count_launch();
-  k_x_fwd<V><<<blocks, kThreads, sm, st>>>(g, s, tw, in, scale, W, done);
+  k_x_fwd<V><<<blocks, kThreads, sm, st>>>(g, s, tw, in, scale, W, done, partials, sc, sum_out);
 }
 
 template <typename V>
@@ -407,26 +416,27 @@ template <typename V>
 void launch_x_inv(const PassGeom& g, const FftSched& s, const V* tw, const V* W, double* out,
                   const double* out_scale, const double* dot_with, double* partials,
                   PcgScalars* sc, int counter_slot, double* dot_out, const int* done,
-                  cudaStream_t st) {
+                  cudaStream_t st, double* partials2, double* wsum_out) {
   const int npairs = (g.nrows + 1) / 2;
   const int blocks = (npairs + g.lines_x - 1) / g.lines_x;
   const size_t sm = x_lines_smem_bytes(s.L, g.lines_x, sizeof(V));
   set_smem(k_x_inv<V>, sm);
   count_launch();
   k_x_inv<V><<<blocks, kThreads, sm, st>>>(g, s, tw, W, out, out_scale, dot_with, partials, sc,
-                                           counter_slot, dot_out, done);
+                                           counter_slot, dot_out, done, partials2, wsum_out);
 }
 
 #define GPS_INSTANTIATE(V)                                                                        \
   template void launch_x_fwd<V>(const PassGeom&, const FftSched&, const V*, const double*,        \
-                                const double*, V*, const int*, cudaStream_t);                     \
+                                const double*, V*, const int*, cudaStream_t, double*, PcgScalars*, \
+                                double*);                                                          \
   template void launch_y<V>(const PassGeom&, const FftSched&, const V*, V*, bool, const int*,     \
                             cudaStream_t);                                                        \
   template void launch_z<V>(const PassGeom&, const FftSched&, const V*, V*, const double*, double, \
                             int, double*, const int*, cudaStream_t);                              \
   template void launch_x_inv<V>(const PassGeom&, const FftSched&, const V*, const V*, double*,    \
                                 const double*, const double*, double*, PcgScalars*, int, double*, \
-                                const int*, cudaStream_t);
+                                const int*, cudaStream_t, double*, double*);
 
 GPS_INSTANTIATE(double2)
 GPS_INSTANTIATE(float2)

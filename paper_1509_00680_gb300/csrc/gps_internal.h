@@ -25,7 +25,8 @@ struct FftSched {
 // the reducing kernels, read by every block of the following kernels.
 struct PcgScalars {
   double vr, vr_prev, pAp, alpha, beta, rr, rr0, tol2;
-  double mu_sum;        // periodic: sum of s*r over the grid (k = 0 of the spectrum)
+  double mu_sum;        // periodic: sum of s*r over the grid (FP64, x pass)
+  double wsum;          // periodic: sum of w = sqrt(eps) v over the grid (x inverse pass)
   double background;    // periodic GPe: mean of rho removed
   double aux[8];        // scratch results of one-off reductions
   int iter, done, status, max_iter;
@@ -34,7 +35,8 @@ struct PcgScalars {
   unsigned int counter[8];
 };
 
-enum Counter { CNT_VR = 0, CNT_PAP = 1, CNT_RR = 2, CNT_AUX = 3, CNT_AUX2 = 4 };
+enum Counter { CNT_VR = 0, CNT_PAP = 1, CNT_RR = 2, CNT_AUX = 3, CNT_AUX2 = 4, CNT_MU = 5,
+               CNT_WSUM = 6 };
 
 // Precomputed factors of the ionic charge (Eqs. rhoions, ionsconcPB).
 struct IonParams {
@@ -66,7 +68,8 @@ struct SpecBuf {
 // Forward x pass: rows of in (optionally scaled by scale) -> half spectra.
 template <typename V>
 void launch_x_fwd(const PassGeom& g, const FftSched& s, const V* tw, const double* in,
-                  const double* scale, V* W, const int* done, cudaStream_t st);
+                  const double* scale, V* W, const int* done, cudaStream_t st,
+                  double* partials = nullptr, PcgScalars* sc = nullptr, double* sum_out = nullptr);
 template <typename V>
 void launch_y(const PassGeom& g, const FftSched& s, const V* tw, V* W, bool inverse,
               const int* done, cudaStream_t st);
@@ -77,7 +80,7 @@ template <typename V>
 void launch_x_inv(const PassGeom& g, const FftSched& s, const V* tw, const V* W, double* out,
                   const double* out_scale, const double* dot_with, double* partials,
                   PcgScalars* sc, int counter_slot, double* dot_out, const int* done,
-                  cudaStream_t st);
+                  cudaStream_t st, double* partials2 = nullptr, double* wsum_out = nullptr);
 size_t x_lines_smem_bytes(int L, int lines, size_t vbytes);
 
 // ---- kernels.cu ------------------------------------------------------------

@@ -144,17 +144,23 @@ __global__ void k_init(const double* __restrict__ rho, double* __restrict__ r,
 
 // p = v + beta p ; A p = -(q + lambda) v - 4 pi r [+ 4 pi <s r> sqrt(eps)] + beta A p ;
 // partial (p, A p).  beta = (v,r)/(v,r)_prev, beta_0 = 0 (Algorithm 2).
+// Periodic GPe (project != 0): v is first put back on the gauge subspace
+// sum sqrt(eps) v = 0 by v -= c s, c = <sqrt(eps) v>, and (v, r) is corrected
+// by -c (s, r); in exact arithmetic c = 0 (the vacuum solve drops k = 0), the
+// projection only removes the rounding of the spectrum passes.
 __global__ void k_update_p(const double* __restrict__ v, const double* __restrict__ r,
                            const double* __restrict__ qlam, const double* __restrict__ sqrt_eps,
-                           double* __restrict__ p, double* __restrict__ Ap, size_t n, double inv_n,
-                           int periodic, double* partials, PcgScalars* sc) {
+                           const double* __restrict__ s, double* __restrict__ p,
+                           double* __restrict__ Ap, size_t n, double inv_n, int periodic,
+                           int project, double* partials, PcgScalars* sc) {
   if (sc->done) return;
-  const double vr = sc->vr;
+  const double c = project ? sc->wsum * inv_n : 0.0;
+  const double vr = project ? sc->vr - c * sc->mu_sum : sc->vr;
   const double beta = sc->iter == 0 ? 0.0 : vr / sc->vr_prev;
   const double mu4pi = periodic ? kFourPi * sc->mu_sum * inv_n : 0.0;
   double acc = 0.0;
   GRID_STRIDE(i, n) {
-    const double vi = v[i];
+    const double vi = project ? v[i] - c * s[i] : v[i];
     double av = -qlam[i] * vi - kFourPi * r[i];
     if (periodic) av += mu4pi * sqrt_eps[i];
     const double pi_ = vi + beta * p[i];
@@ -166,6 +172,7 @@ __global__ void k_update_p(const double* __restrict__ v, const double* __restric
   if (grid_reduce(acc, partials, &sc->counter[CNT_PAP], &sc->pAp) && threadIdx.x == 0) {
     const double pap = sc->pAp;
     sc->beta = beta;
+    sc->vr = vr;
     sc->vr_prev = vr;
     if (!(pap < 0.0) || !isfinite(pap) || !isfinite(vr)) {
       sc->status = GPS_ERR_BREAKDOWN;
@@ -454,11 +461,11 @@ void launch_init(const double* rho, double* r, double* phi, double* p, double* A
 }
 
 void launch_update_p(const double* v, const double* r, const double* qlam, const double* sqrt_eps,
-                     double* p, double* Ap, size_t n, int periodic, double* partials,
-                     PcgScalars* sc, cudaStream_t st) {
+                     const double* s, double* p, double* Ap, size_t n, int periodic, int project,
+                     double* partials, PcgScalars* sc, cudaStream_t st) {
   count_launch();
-  k_update_p<<<grid_blocks(n, kT), kT, 0, st>>>(v, r, qlam, sqrt_eps, p, Ap, n, 1.0 / (double)n,
-                                                periodic, partials, sc);
+  k_update_p<<<grid_blocks(n, kT), kT, 0, st>>>(v, r, qlam, sqrt_eps, s, p, Ap, n, 1.0 / (double)n,
+                                                periodic, project, partials, sc);
 }
 
 void launch_update_r(double* phi, double* r, const double* p, const double* Ap, size_t n,

@@ -27,8 +27,8 @@ void launch_init(const double* rho, double* r, double* phi, double* p, double* A
                  double tol_abs, double tol_rel, int max_iter, double* partials, PcgScalars* sc,
                  int zero_phi, const double* bg_sum, cudaStream_t st);
 void launch_update_p(const double* v, const double* r, const double* qlam, const double* sqrt_eps,
-                     double* p, double* Ap, size_t n, int periodic, double* partials,
-                     PcgScalars* sc, cudaStream_t st);
+                     const double* s, double* p, double* Ap, size_t n, int periodic, int project,
+                     double* partials, PcgScalars* sc, cudaStream_t st);
 void launch_update_r(double* phi, double* r, const double* p, const double* Ap, size_t n,
                      double* partials, PcgScalars* sc, cudaStream_t st);
 void launch_fp_source(const double* rho, const double* rions, const double* qlam, const double* phi,

@@ -299,7 +299,8 @@ def test_full_surface_lpb(gps, ctx):
 @pytest.mark.parametrize("wl,kw,kind", [
     (4, dict(n=64, count=12, margin=6.0, kind="gpe"), "gpe"),
     (2, dict(n=48, count=8), "gpe"),
-    (3, dict(nxy=32, nz=48, count=6), "lpb"),
+    (3, dict(nxy=32, nz=96, count=6), "lpb"),
+    (2, dict(n=96, count=12), "gpe"),
 ])
 def test_mixed_precision_error(gps, ctx, wl, kw, kind):
     """FP32 spectrum inside the FP64 PCG: relative L2 error against the FP64
