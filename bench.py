@@ -20,6 +20,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -56,10 +57,10 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index):
+    def __init__(self, device_index, path=None):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), "gps_bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
         try:
@@ -175,7 +176,7 @@ def run_ours(args, ws, rank, local):
     dom = max(warm, key=lambda k: warm[k][1])
     shares = {k: round(v[1] / sum(w[1] for w in warm.values()), 4) for k, v in warm.items()}
     barrier()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_log)
     clocks.start()
     ctx.set_profiling([dom])             # only the dominant kernel is event-timed
     ctx.get_profile(reset=True)
@@ -208,6 +209,8 @@ def run_ours(args, ws, rank, local):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(ctx, g, p, npts, opts, flush, args)
+    mixed = None if args.no_mixed else run_mixed(ctx, g, rho, eps, phi, flush, args, gps, total_ms / args.steps)
+    serving = None if args.no_serving else run_serving(gps, local, args)
 
     # roofline of the dominant kernel (largest share of kernel time in warm-up)
     n_l, t_l = prof[dom]
@@ -227,6 +230,8 @@ def run_ours(args, ws, rank, local):
         "config": config_dict({"pcg_iters_per_solve": int(statistics.median(iters))}),
         "solves_per_s": ws * args.steps / (total_ms / 1e3),
         "e2e": e2e,
+        "mixed": mixed,
+        "serving": serving,
         "roofline": roof,
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -239,6 +244,91 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_mixed(ctx, g, rho, eps, phi64, flush, args, gps, fp64_ms):
+    """The same workload with the FP32 spectrum inside the FP64 PCG: solves/s,
+    relative L2 error against the FP64 GPU result, FP64 certificate."""
+    import torch
+    stream = torch.cuda.current_stream()
+    phi = torch.empty_like(phi64)
+    o = gps.default_opts(tol_abs=1e-10, precision=gps.GPS_MIXED)
+    ctx.gpe_solve(g, rho, eps, phi, o)
+    ms, reps = 0.0, []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps.append(ctx.gpe_solve(g, rho, eps, phi, o))
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    err = (torch.linalg.norm(phi - phi64) / torch.linalg.norm(phi64)).item()
+    return {"solves_per_s": args.steps / (ms / 1e3), "ms_per_solve": ms / args.steps,
+            "speedup_vs_fp64": fp64_ms / (ms / args.steps), "rel_l2_err_vs_fp64": err,
+            "certificate": reps[-1].fixed_point_res, "pcg_iters": reps[-1].iters,
+            "fp64_iters": reps[-1].fp64_iters, "switch": 1e-2}
+
+
+def run_serving(gps, device, args, count=None):
+    """Bounded sample of the serving workload: requests drawn like the
+    512-request stream (edges {48,64,96,128,192}, BC and problem mixed,
+    5-80 charges, 0.01-1 M), Poisson arrivals at 1.5x the capacity measured
+    by a batch solve of the same requests, 120 GB admission budget."""
+    import threading
+    import synth
+    count = count or args.serving_count
+    desc = synth.serving_stream(count=count, seed=1005)
+    reqs = []
+    for edge, bc, kind, seed in desc:
+        rng = np.random.default_rng(seed)
+        p = synth.serving_request(rng, edge, bc, kind)
+        el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, 300.0, p.eps0)
+        reqs.append((p, kind, el))
+
+    def make(i):
+        p, kind, el = reqs[i]
+        rho = np.ascontiguousarray(p.rho.ravel())
+        eps = np.ascontiguousarray(p.eps.ravel())
+        phi = np.zeros(p.grid.npts)
+        r = gps.make_request(gps.grid_from(p.grid), kind, rho, eps, phi, el,
+                             gps.default_opts(tol_abs=1e-10, tol_outer=1e-10, max_iter=3000))
+        return r, (rho, eps, phi)
+
+    ctx = gps.Context(device, 120 << 30)
+    made = [make(i) for i in range(count)]
+    gps.batch_solve(ctx, [m[0] for m in made], allow=(0, 3))       # warm-up: plans, graphs
+    t0 = time.perf_counter()
+    gps.batch_solve(ctx, [m[0] for m in made], allow=(0, 3))
+    capacity = count / (time.perf_counter() - t0)
+    ctx.close()
+    srv = gps.Server(device, hbm_budget_bytes=120 << 30)
+    rate = 1.5 * capacity
+    rng = np.random.default_rng(77)
+    tickets, keep = [], []
+    start = time.perf_counter()
+
+    def producer():
+        for i in range(count):
+            r, hold = made[i]
+            keep.append(hold)
+            tickets.append(srv.submit(r, keep=hold))
+            time.sleep(float(rng.exponential(1.0 / rate)))
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    results = [srv.wait(t) for t in tickets]
+    wall = time.perf_counter() - start
+    stats = srv.stats()
+    srv.close()
+    lat = sorted(rep.time_ms for _, rep in results)
+    ok = sum(1 for s, _ in results if s == 0)
+    return {"requests": count, "ok": ok, "arrival_rate_per_s": rate, "batch_capacity_solves_per_s": capacity,
+            "solves_per_s": count / wall, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_concurrent": stats["max_concurrent"],
+            "pool_bytes": stats["bytes_in_use"]}
 
 
 def run_e2e(ctx, g, p, npts, opts, flush, args):
@@ -314,6 +404,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--clocks-log", default=None, help="keep the nvidia-smi samples of the timed region here")
+    ap.add_argument("--serving-count", type=int, default=24)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -49,7 +49,16 @@ typedef enum {
   GPS_BC_SURFACE = 2     /* periodic in x and y, free in z (2x padded in z) */
 } gps_bc;
 
-typedef enum { GPS_FP64 = 0, GPS_MIXED = 1 } gps_precision;
+/* Arithmetic of the spectrum passes (the vacuum solve inside the
+ * preconditioner); every vector, dot product, alpha/beta and the ionic term
+ * are FP64 in all modes.
+ *   GPS_FP64        FP64 spectrum.
+ *   GPS_MIXED       FP64 spectrum until ||r|| <= mixed_switch ||r_0||, then FP32.
+ *   GPS_DF64        double-float spectrum: each value the unevaluated sum of
+ *                   two floats (about 48 significant bits), computed on the
+ *                   FP32 pipe, which on GB300 issues 64x the FP64 rate.
+ *   GPS_MIXED_DF64  double-float spectrum until the switch, then FP32. */
+typedef enum { GPS_FP64 = 0, GPS_MIXED = 1, GPS_DF64 = 2, GPS_MIXED_DF64 = 3 } gps_precision;
 typedef enum { GPS_GPE = 0, GPS_LPB = 1, GPS_NLPB = 2 } gps_problem;
 typedef enum { GPS_OUTER_NEWTON = 0, GPS_OUTER_PRINTED = 1 } gps_outer_mode;
 
@@ -175,7 +184,8 @@ int gps_vacuum_solve(gps_ctx* ctx, const gps_grid* grid, const double* sigma_dev
                      double* w_dev, void* cuda_stream);
 
 /* Step S3, the preconditioner of Eq. (PCGdef): v = s S(s r) for a given
- * s = eps^-1/2.  precision = GPS_MIXED runs the FFT passes in FP32. */
+ * s = eps^-1/2.  precision: GPS_FP64, GPS_MIXED (FFT passes in FP32) or
+ * GPS_DF64 (FFT passes in double-float). */
 int gps_precondition(gps_ctx* ctx, const gps_grid* grid, const double* s_dev,
                      const double* r_dev, double* v_dev, int precision,
                      void* cuda_stream);
@@ -186,6 +196,54 @@ int gps_precondition(gps_ctx* ctx, const gps_grid* grid, const double* s_dev,
 int gps_ionic_charge(gps_ctx* ctx, const gps_grid* grid, const double* phi_dev,
                      const double* eps_dev, const gps_electrolyte* el,
                      double* out_dev, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Batched and served solves.  A request carries its own grid, problem,
+ * electrolyte and options and host arrays (rho and eps are read when the
+ * request is admitted; phi is written when it completes; all three must stay
+ * valid until then).  Requests with the same grid (shape, spacing, BC) share
+ * a pool of slots: one launch sequence advances every slot of a pool by a
+ * few PCG iterations (Algorithm 2), each slot at its own stage (setup,
+ * iterations, the outer steps of Algorithm 4, certificate).  A request is
+ * admitted into a free slot as soon as one frees up and device memory
+ * allows, while the other slots keep iterating (continuous batching); pools
+ * of different grids run on their own streams and overlap on the device.
+ * Every slot reduces in a fixed order, so a result does not depend on which
+ * other requests shared its launches.
+ */
+typedef struct {
+  gps_grid grid;
+  int kind;                 /* gps_problem */
+  gps_electrolyte el;       /* ignored for GPS_GPE */
+  gps_opts opts;
+  const double* rho_host;
+  const double* eps_host;
+  double* phi_host;
+} gps_request;
+
+/* Solve `count` requests on the context's device with continuous batching,
+ * returning when all are done; reps[i] receives request i's report (its
+ * time_ms is the latency from the call to that request's completion).
+ * Returns GPS_OK if every request succeeded, else the first failing status. */
+int gps_batch_solve(gps_ctx* ctx, int count, const gps_request* reqs, gps_report* reps);
+
+/* Asynchronous serving loop: a host thread admits submitted requests
+ * against the HBM budget (hbm_budget_bytes, 0 = no cap) into pools of at
+ * most max_slots slots (0 = automatic by grid size) and drives them.
+ * gps_server_submit returns a ticket; gps_server_poll returns GPS_PENDING
+ * until the request is done, then its final status (and report, whose
+ * time_ms is the submit-to-completion latency); gps_server_wait blocks.
+ * A ticket can be polled or waited on until it has returned a final status
+ * once. */
+typedef struct gps_server gps_server;
+int gps_server_create(gps_server** out, int device, size_t hbm_budget_bytes, int max_slots);
+int gps_server_submit(gps_server* srv, const gps_request* req, unsigned long long* ticket);
+int gps_server_poll(gps_server* srv, unsigned long long ticket, gps_report* rep);
+int gps_server_wait(gps_server* srv, unsigned long long ticket, gps_report* rep);
+/* Device bytes held by the server's pools and the largest number of
+ * requests that were in slots at the same time. */
+int gps_server_stats(gps_server* srv, size_t* bytes_in_use, int* max_concurrent);
+void gps_server_destroy(gps_server* srv);
 
 /* Vacuum Poisson solve w = S(sigma) (as gps_vacuum_solve) for callers that
  * cannot allocate device memory -- for example a plugin whose host

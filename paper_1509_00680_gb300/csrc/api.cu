@@ -1,21 +1,35 @@
-// C ABI of the solver (include/gps.h): context, cached plans, and the
-// drivers of Algorithm 2 (PCG) and Algorithm 4 (nonlinear PB outer loop).
+// C ABI of the solver (include/gps.h) and its host engine.
 //
-// A plan is everything that depends on (grid, spacing, BC): FFT schedules
-// and twiddles, the Green's-function table, the spectrum workspace and the
-// PCG vectors.  Plans are cached per context and evicted least-recently-used
-// under the context's HBM budget.
+// Shape: everything that depends on (grid, spacing, BC) only -- FFT
+//   schedules, twiddles, Green's-function and Laplacian tables.
+// Pool: `cap` slots of one shape, each with strided vectors, a spectrum
+//   workspace, reduction partials and a SlotState; one round launches every
+//   stage of the device phase machine (kernels.cu) once and `m` PCG
+//   iterations, each kernel acting on the slots in its phase.
+// Engine: pools of one device, a queue of requests, admission into free
+//   slots under the HBM budget, rounds on every busy pool (one stream per
+//   pool, so pools overlap on the device) and collection of finished slots.
+// Single solves run in a one-slot pool per shape, driven on the caller's
+// stream; batches and the server run an Engine.
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
+#include "device_util.cuh"
 #include "gps_internal.h"
 #include "kernels.h"
 
@@ -23,7 +37,15 @@ using namespace gps;
 
 namespace {
 
-// ---------------------------------------------------------------- helpers --
+struct CudaError {};
+inline void ck(cudaError_t e) {
+  if (e != cudaSuccess) throw CudaError{};
+}
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
 
 bool factorable(int L) {
   int r = L;
@@ -32,25 +54,39 @@ bool factorable(int L) {
   return r == 1;
 }
 
-bool make_sched(int L, FftSched* s) {
+// Stockham schedule of length L.  order 0: radix 8 first, then 4/2, 5, 3;
+// order 1: the radix-2/4 remainder first, then the 8s; order 2: radix 4
+// throughout (then 2), then 5 and 3.
+bool make_sched(int L, FftSched* s, int order = 0) {
   if (L < 2 || L > kMaxLen || !factorable(L)) return false;
   std::memset(s, 0, sizeof(*s));
   s->L = L;
-  int rem = L, ns = 1, k = 0;
-  auto push = [&](int R) {
-    s->radix[k] = R;
+  std::vector<int> rad;
+  int rem = L;
+  int p2 = 0;
+  while (rem % 2 == 0) { rem /= 2; ++p2; }
+  std::vector<int> twos;
+  if (order == 2) {
+    while (p2 >= 2) { twos.push_back(4); p2 -= 2; }
+    if (p2) twos.push_back(2);
+  } else {
+    while (p2 >= 3) { twos.push_back(8); p2 -= 3; }
+    if (p2 == 2) twos.push_back(4);
+    if (p2 == 1) twos.push_back(2);
+    if (order == 1) std::reverse(twos.begin(), twos.end());
+  }
+  rad = twos;
+  while (rem % 5 == 0) { rad.push_back(5); rem /= 5; }
+  while (rem % 3 == 0) { rad.push_back(3); rem /= 3; }
+  if (rem != 1 || (int)rad.size() > kMaxStages) return false;
+  int ns = 1;
+  for (size_t k = 0; k < rad.size(); ++k) {
+    s->radix[k] = rad[k];
     s->ns[k] = ns;
-    ns *= R;
-    rem /= R;
-    ++k;
-  };
-  while (rem % 8 == 0) push(8);
-  if (rem % 4 == 0) push(4);
-  if (rem % 2 == 0) push(2);
-  while (rem % 5 == 0) push(5);
-  while (rem % 3 == 0) push(3);
-  s->nst = k;
-  return rem == 1 && k <= kMaxStages;
+    ns *= rad[k];
+  }
+  s->nst = (int)rad.size();
+  return true;
 }
 
 // Order-16 central second-derivative coefficients (exact formula, long double):
@@ -73,195 +109,6 @@ Fd16 fd16_coeffs() {
   return c;
 }
 
-struct CudaError {};
-
-inline void ck(cudaError_t e) {
-  if (e != cudaSuccess) throw CudaError{};
-}
-
-struct Dev {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
-}  // namespace
-
-// ------------------------------------------------------------------ plans --
-
-struct FftLen {
-  FftSched sched;
-  double2* tw64 = nullptr;
-  float2* tw32 = nullptr;
-};
-
-struct Plan {
-  int nx, ny, nz, bc;
-  double hx, hy, hz;
-  int Px, Py, Pz, Hx;
-  size_t n;
-  PassGeom g64, g32;
-  FftLen fx, fy, fz;
-  double* table = nullptr;
-  double* lap_table = nullptr;
-  double2* W64 = nullptr;
-  float2* W32 = nullptr;
-  double *s = nullptr, *sq = nullptr, *q = nullptr, *qlam = nullptr;
-  double *r = nullptr, *p = nullptr, *Ap = nullptr, *v = nullptr;
-  double *rions = nullptr, *rp = nullptr, *fresh = nullptr, *lam = nullptr, *dphi = nullptr,
-         *src = nullptr;
-  double *io_rho = nullptr, *io_eps = nullptr, *io_phi = nullptr;
-  double* partials = nullptr;
-  double* partials2 = nullptr;
-  PcgScalars* sc = nullptr;
-  PcgScalars* sc_host = nullptr;
-  std::vector<void*> allocs;
-  size_t bytes = 0;
-  unsigned long long last_use = 0;
-
-  template <typename T>
-  T* alloc(size_t count) {
-    void* ptr = nullptr;
-    const size_t b = count * sizeof(T);
-    if (cudaMalloc(&ptr, b) != cudaSuccess) throw std::bad_alloc();
-    allocs.push_back(ptr);
-    bytes += b;
-    return static_cast<T*>(ptr);
-  }
-  ~Plan() {
-    for (void* a : allocs) cudaFree(a);
-    if (sc_host) cudaFreeHost(sc_host);
-  }
-};
-
-// Opt-in per-kernel timing with CUDA events on the launching stream.
-struct Profiler {
-  bool on = false;
-  int mask = 0;
-  struct Rec { int kind; cudaEvent_t a, b; };
-  std::vector<Rec> pending;
-  std::vector<cudaEvent_t> pool;
-  long long launches[GPS_PROFILE_KINDS] = {0};
-  double ms[GPS_PROFILE_KINDS] = {0};
-  cudaEvent_t get() {
-    if (!pool.empty()) {
-      cudaEvent_t e = pool.back();
-      pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    return e;
-  }
-  void resolve() {
-    if (pending.empty()) return;
-    cudaEventSynchronize(pending.back().b);
-    for (auto& r : pending) {
-      float t = 0.f;
-      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
-        launches[r.kind] += 1;
-        ms[r.kind] += t;
-      }
-      pool.push_back(r.a);
-      pool.push_back(r.b);
-    }
-    pending.clear();
-  }
-  // Drop the records of loop kernels (kinds 0..6) launched after the PCG had
-  // converged (they return at once) -- keep the first `iters` of each kind.
-  void trim_loop(size_t from, int iters) {
-    int seen[GPS_PROFILE_KINDS] = {0};
-    std::vector<Rec> keep(pending.begin(), pending.begin() + from);
-    for (size_t i = from; i < pending.size(); ++i) {
-      const Rec& r = pending[i];
-      if (r.kind < 7 && seen[r.kind]++ >= iters) {
-        pool.push_back(r.a);
-        pool.push_back(r.b);
-      } else {
-        keep.push_back(r);
-      }
-    }
-    pending.swap(keep);
-  }
-  ~Profiler() {
-    for (auto& r : pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
-    for (auto e : pool) cudaEventDestroy(e);
-  }
-};
-
-static thread_local Profiler* t_prof = nullptr;
-
-template <typename F>
-static void timed(int kind, cudaStream_t st, F&& f) {
-  if (!t_prof || !t_prof->on || !(t_prof->mask & (1 << kind))) {
-    f();
-    return;
-  }
-  cudaEvent_t a = t_prof->get(), b = t_prof->get();
-  cudaEventRecord(a, st);
-  f();
-  cudaEventRecord(b, st);
-  t_prof->pending.push_back({kind, a, b});
-}
-
-struct gps_ctx {
-  Profiler prof;
-  int device = 0;
-  size_t budget = 0;
-  std::vector<std::unique_ptr<Plan>> plans;
-  unsigned long long clock = 0;
-  size_t in_use() const {
-    size_t b = 0;
-    for (auto& p : plans) b += p->bytes;
-    return b;
-  }
-};
-
-namespace {
-
-int validate_grid(const gps_grid* g) {
-  if (!g) return GPS_ERR_INVALID;
-  if (g->nx < 4 || g->ny < 4 || g->nz < 4) return GPS_ERR_INVALID;
-  if (!(g->hx > 0) || !(g->hy > 0) || !(g->hz > 0)) return GPS_ERR_INVALID;
-  if (g->bc < GPS_BC_FREE || g->bc > GPS_BC_SURFACE) return GPS_ERR_INVALID;
-  const bool fx = g->bc == GPS_BC_FREE, fy = fx, fz = g->bc != GPS_BC_PERIODIC;
-  const int Px = fx ? 2 * g->nx : g->nx, Py = fy ? 2 * g->ny : g->ny, Pz = fz ? 2 * g->nz : g->nz;
-  for (int P : {Px, Py, Pz})
-    if (P % 2 || P > kMaxLen || !factorable(P)) return GPS_ERR_INVALID;
-  if (g->bc == GPS_BC_FREE) {
-    const double R = std::sqrt(std::pow(g->nx * g->hx, 2) + std::pow(g->ny * g->hy, 2) +
-                               std::pow(g->nz * g->hz, 2));
-    if (4 * g->nx * g->hx < g->nx * g->hx + R || 4 * g->ny * g->hy < g->ny * g->hy + R ||
-        4 * g->nz * g->hz < g->nz * g->hz + R)
-      return GPS_ERR_INVALID;   // aspect ratio too large for the 4x oversampled kernel
-  }
-  return GPS_OK;
-}
-
-int batch_lines(int L, int units) {
-  int b = 2048 / L;
-  if (b < 1) b = 1;
-  const int want = units / 304;   // keep >= ~2 CTAs per SM
-  if (want < b) b = want < 1 ? 1 : want;
-  return b;
-}
-
-void fill_twiddles(Plan* P, FftLen* f, int L) {
-  if (!make_sched(L, &f->sched)) throw std::bad_alloc();
-  std::vector<double2> h64(L);
-  std::vector<float2> h32(L);
-  for (int m = 0; m < L; ++m) {
-    const long double ang = 2.0L * 3.141592653589793238462643383279502884L * m / L;
-    h64[m].x = (double)cosl(ang);
-    h64[m].y = (double)-sinl(ang);
-    h32[m].x = (float)h64[m].x;
-    h32[m].y = (float)h64[m].y;
-  }
-  f->tw64 = P->alloc<double2>(L);
-  f->tw32 = P->alloc<float2>(L);
-  ck(cudaMemcpy(f->tw64, h64.data(), L * sizeof(double2), cudaMemcpyHostToDevice));
-  ck(cudaMemcpy(f->tw32, h32.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
-}
-
 // Even (cosine) transform matrix C[k][j] = w_j cos(2 pi j k / M) * scale,
 // j = 0..M/2, k = 0..K-1, w_0 = w_(M/2) = 1, otherwise 2.
 std::vector<double> cosine_matrix(int M, int K, double scale) {
@@ -277,330 +124,46 @@ std::vector<double> cosine_matrix(int M, int K, double scale) {
   return C;
 }
 
-// Free-BC table: h^3 g on the octant from the 4x oversampled truncated-Coulomb
-// transform (three even transforms), then its 2n-periodic transform (three
-// more), normalized by 1/(Px Py Pz).
-void build_free_table(Plan* P, cudaStream_t st) {
-  const int nx = P->nx, ny = P->ny, nz = P->nz;
-  const int Mx = 4 * nx, My = 4 * ny, Mz = 4 * nz;
-  const int mx = Mx / 2 + 1, my = My / 2 + 1, mz = Mz / 2 + 1;
-  const double R = std::sqrt(std::pow(nx * P->hx, 2) + std::pow(ny * P->hy, 2) + std::pow(nz * P->hz, 2));
-  double *ghat = nullptr, *t1 = nullptr, *t2 = nullptr, *g = nullptr, *u1 = nullptr, *u2 = nullptr;
-  double *cx = nullptr, *cy = nullptr, *cz = nullptr, *dx = nullptr, *dy = nullptr, *dz = nullptr;
-  auto tmp = [&](size_t cnt) {
-    void* ptr = nullptr;
-    if (cudaMalloc(&ptr, cnt * sizeof(double)) != cudaSuccess) throw std::bad_alloc();
-    return static_cast<double*>(ptr);
-  };
-  auto up = [&](const std::vector<double>& h) {
-    double* d = tmp(h.size());
-    ck(cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
-    return d;
-  };
-  const int hxo = nx + 1, hyo = ny + 1, hzo = nz + 1;
-  try {
-    ghat = tmp((size_t)mx * my * mz);
-    launch_free_ghat(ghat, mx, my, mz, 2 * kPi / (Mx * P->hx), 2 * kPi / (My * P->hy),
-                     2 * kPi / (Mz * P->hz), R, st);
-    cx = up(cosine_matrix(Mx, hxo, 1.0 / Mx));
-    cy = up(cosine_matrix(My, hyo, 1.0 / My));
-    cz = up(cosine_matrix(Mz, hzo, 1.0 / Mz));
-    t1 = tmp((size_t)mz * my * hxo);
-    launch_axis_matrix(ghat, t1, cx, mz * my, mx, 1, hxo, st);
-    ck(cudaStreamSynchronize(st));
-    cudaFree(ghat);
-    ghat = nullptr;
-    t2 = tmp((size_t)mz * hyo * hxo);
-    launch_axis_matrix(t1, t2, cy, mz, my, hxo, hyo, st);
-    g = tmp((size_t)hzo * hyo * hxo);
-    launch_axis_matrix(t2, g, cz, 1, mz, hyo * hxo, hzo, st);
-    // transform of the 2n-periodic even extension: M = 2n, entries m = 0..n
-    dx = up(cosine_matrix(2 * nx, hxo, 1.0 / (2 * nx)));
-    dy = up(cosine_matrix(2 * ny, hyo, 1.0 / (2 * ny)));
-    dz = up(cosine_matrix(2 * nz, hzo, 1.0 / (2 * nz)));
-    u1 = tmp((size_t)hzo * hyo * hxo);
-    u2 = tmp((size_t)hzo * hyo * hxo);
-    launch_axis_matrix(g, u1, dx, hzo * hyo, hxo, 1, hxo, st);
-    launch_axis_matrix(u1, u2, dy, hzo, hyo, hxo, hyo, st);
-    launch_axis_matrix(u2, P->table, dz, 1, hzo, hyo * hxo, hzo, st);
-    ck(cudaStreamSynchronize(st));
-    ck(cudaGetLastError());
-  } catch (...) {
-    for (double* d : {ghat, t1, t2, g, u1, u2, cx, cy, cz, dx, dy, dz})
-      if (d) cudaFree(d);
-    throw;
-  }
-  for (double* d : {t1, t2, g, u1, u2, cx, cy, cz, dx, dy, dz})
-    if (d) cudaFree(d);
-}
-
-Plan* build_plan(const gps_grid* gr, cudaStream_t st) {
-  auto P = std::make_unique<Plan>();
-  P->nx = gr->nx; P->ny = gr->ny; P->nz = gr->nz; P->bc = gr->bc;
-  P->hx = gr->hx; P->hy = gr->hy; P->hz = gr->hz;
-  const bool fx = gr->bc == GPS_BC_FREE, fz = gr->bc != GPS_BC_PERIODIC;
-  P->Px = fx ? 2 * gr->nx : gr->nx;
-  P->Py = fx ? 2 * gr->ny : gr->ny;
-  P->Pz = fz ? 2 * gr->nz : gr->nz;
-  P->Hx = P->Px / 2 + 1;
-  P->n = (size_t)gr->nx * gr->ny * gr->nz;
-  PassGeom g;
-  g.nx = gr->nx; g.ny = gr->ny; g.nz = gr->nz;
-  g.Px = P->Px; g.Py = P->Py; g.Pz = P->Pz; g.Hx = P->Hx;
-  g.nrows = gr->ny * gr->nz;
-  g.lines_x = batch_lines(P->Px, (g.nrows + 1) / 2);
-  g.tile_y = batch_lines(P->Py, P->Hx * gr->nz);
-  g.tile_z = batch_lines(P->Pz, P->Hx * P->Py);
-  P->g64 = g;
-  P->g32 = g;
-  fill_twiddles(P.get(), &P->fx, P->Px);
-  fill_twiddles(P.get(), &P->fy, P->Py);
-  fill_twiddles(P.get(), &P->fz, P->Pz);
-  const int hy = P->Py / 2 + 1, hz = P->Pz / 2 + 1;
-  const size_t tab = (size_t)P->Hx * hy * hz;
-  const double inv_n = 1.0 / ((double)P->Px * P->Py * P->Pz);
-  P->table = P->alloc<double>(tab);
-  if (gr->bc == GPS_BC_PERIODIC) {
-    P->lap_table = P->alloc<double>(tab);
-    launch_table_periodic(P->table, P->lap_table, P->Hx, hy, hz, 2 * kPi / (P->Px * gr->hx),
-                          2 * kPi / (P->Py * gr->hy), 2 * kPi / (P->Pz * gr->hz), inv_n, st);
-  } else if (gr->bc == GPS_BC_SURFACE) {
-    launch_table_surface(P->table, P->Hx, hy, hz, 2 * kPi / (P->Px * gr->hx),
-                         2 * kPi / (P->Py * gr->hy), 2 * kPi / (P->Pz * gr->hz), gr->nz * gr->hz,
-                         inv_n, st);
-  } else {
-    build_free_table(P.get(), st);
-  }
-  P->W64 = P->alloc<double2>((size_t)P->Hx * P->Py * gr->nz);
-  const size_t n = P->n;
-  P->s = P->alloc<double>(n);
-  P->sq = P->alloc<double>(n);
-  P->q = P->alloc<double>(n);
-  P->qlam = P->alloc<double>(n);
-  P->r = P->alloc<double>(n);
-  P->p = P->alloc<double>(n);
-  P->Ap = P->alloc<double>(n);
-  P->v = P->alloc<double>(n);
-  size_t maxblocks = 152 * 8;
-  const size_t xb = ((g.nrows + 1) / 2 + g.lines_x - 1) / g.lines_x;
-  if (xb > maxblocks) maxblocks = xb;
-  P->partials = P->alloc<double>(maxblocks);
-  P->partials2 = P->alloc<double>(maxblocks);
-  P->sc = P->alloc<PcgScalars>(1);
-  ck(cudaMemsetAsync(P->sc, 0, sizeof(PcgScalars), st));
-  ck(cudaMallocHost((void**)&P->sc_host, sizeof(PcgScalars)));
-  ck(cudaStreamSynchronize(st));
-  ck(cudaGetLastError());
-  return P.release();
-}
-
-void ensure_nl(Plan* P) {
-  if (P->rions) return;
-  P->rions = P->alloc<double>(P->n);
-  P->rp = P->alloc<double>(P->n);
-  P->fresh = P->alloc<double>(P->n);
-  P->lam = P->alloc<double>(P->n);
-  P->dphi = P->alloc<double>(P->n);
-  P->src = P->alloc<double>(P->n);
-}
-
-void ensure_io(Plan* P) {
-  if (P->io_rho) return;
-  P->io_rho = P->alloc<double>(P->n);
-  P->io_eps = P->alloc<double>(P->n);
-  P->io_phi = P->alloc<double>(P->n);
-}
-
-void ensure_w32(Plan* P) {
-  if (!P->W32) P->W32 = P->alloc<float2>((size_t)P->Hx * P->Py * P->nz);
-}
-
-int get_plan(gps_ctx* c, const gps_grid* gr, cudaStream_t st, Plan** out) {
-  int v = validate_grid(gr);
-  if (v != GPS_OK) return v;
-  ++c->clock;
-  for (auto& p : c->plans) {
-    if (p->nx == gr->nx && p->ny == gr->ny && p->nz == gr->nz && p->bc == gr->bc &&
-        p->hx == gr->hx && p->hy == gr->hy && p->hz == gr->hz) {
-      p->last_use = c->clock;
-      *out = p.get();
-      return GPS_OK;
-    }
-  }
-  Plan* P = nullptr;
-  try {
-    P = build_plan(gr, st);
-  } catch (std::bad_alloc&) {
-    return GPS_ERR_NOMEM;
-  } catch (CudaError&) {
-    return GPS_ERR_CUDA;
-  }
-  // evict least-recently-used plans while over budget
-  while (c->budget && c->in_use() + P->bytes > c->budget && !c->plans.empty()) {
-    size_t lru = 0;
-    for (size_t i = 1; i < c->plans.size(); ++i)
-      if (c->plans[i]->last_use < c->plans[lru]->last_use) lru = i;
-    c->plans.erase(c->plans.begin() + lru);
-  }
-  if (c->budget && P->bytes > c->budget) {
-    delete P;
-    return GPS_ERR_NOMEM;
-  }
-  P->last_use = c->clock;
-  c->plans.emplace_back(P);
-  *out = P;
-  return GPS_OK;
-}
-
-// ------------------------------------------------------------- pipelines --
-
-// Vacuum solve on the spectrum pipeline: out = out_scale * S(in_scale * in),
-// with `table` the normalized octant multiplier.  Optionally reduces
-// (out, dot_with) into sc->vr and records the k = 0 sum in sc->mu_sum.
-template <typename V>
-void vacuum_pipeline(Plan* P, const double* in, const double* in_scale, const double* table,
-                     double k0, int use_k0, double* out, const double* out_scale,
-                     const double* dot_with, bool track, cudaStream_t st, bool gauge = false) {
-  V* W;
-  const V *twx, *twy, *twz;
-  if constexpr (sizeof(V) == sizeof(double2)) {
-    W = reinterpret_cast<V*>(P->W64);
-    twx = reinterpret_cast<const V*>(P->fx.tw64);
-    twy = reinterpret_cast<const V*>(P->fy.tw64);
-    twz = reinterpret_cast<const V*>(P->fz.tw64);
-  } else {
-    W = reinterpret_cast<V*>(P->W32);
-    twx = reinterpret_cast<const V*>(P->fx.tw32);
-    twy = reinterpret_cast<const V*>(P->fy.tw32);
-    twz = reinterpret_cast<const V*>(P->fz.tw32);
-  }
-  const PassGeom& g = P->g64;
-  const int* done = track ? &P->sc->done : nullptr;
-  const bool periodic_track = track && P->bc == GPS_BC_PERIODIC;
-  timed(0, st, [&] {
-    launch_x_fwd<V>(g, P->fx.sched, twx, in, in_scale, W, done, st, P->partials, P->sc,
-                    periodic_track ? &P->sc->mu_sum : nullptr);
-  });
-  timed(1, st, [&] { launch_y<V>(g, P->fy.sched, twy, W, false, done, st); });
-  timed(2, st, [&] { launch_z<V>(g, P->fz.sched, twz, W, table, k0, use_k0, nullptr, done, st); });
-  timed(3, st, [&] { launch_y<V>(g, P->fy.sched, twy, W, true, done, st); });
-  timed(4, st, [&] {
-    launch_x_inv<V>(g, P->fx.sched, twx, W, out, out_scale, dot_with, dot_with ? P->partials : nullptr,
-                    P->sc, CNT_VR, &P->sc->vr, done, st, P->partials2,
-                    gauge ? &P->sc->wsum : nullptr);
-  });
-}
-
-void read_scalars(Plan* P, cudaStream_t st) {
-  ck(cudaMemcpyAsync(P->sc_host, P->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
-  ck(cudaStreamSynchronize(st));
-}
-
-// S1: s, sqrt(eps), q (spectral for periodic, FD-16 otherwise).
-int setup_fields(Plan* P, const double* eps, cudaStream_t st) {
-  timed(7, st, [&] { launch_setup_s(eps, P->s, P->sq, P->n, P->sc, st); });
-  if (P->bc == GPS_BC_PERIODIC) {
-    vacuum_pipeline<double2>(P, P->sq, nullptr, P->lap_table, 0.0, 0, P->q, P->sq, nullptr, false, st);
-  } else {
-    const int per_xy = P->bc == GPS_BC_SURFACE ? 1 : 0;   // surface: x, y wrap; z free
-    launch_fd16_q(P->sq, P->q, P->nx, P->ny, P->nz, P->hx, P->hy, P->hz, per_xy, per_xy, 0,
-                  fd16_coeffs(), st);
-  }
-  return GPS_OK;
-}
-
-struct PcgResult {
-  int status, iters, fp64_iters;
-  double res0, res, background;
-};
-
-// Algorithm 2 from phi = 0 on the current plan state: operator term `qlam`
-// (q + lambda), source rho.  Iterations are enqueued in chunks; the device
-// sets `done`, after which every queued kernel returns at once.
-PcgResult run_pcg(Plan* P, const double* rho, double* phi, const double* qlam, double k0, int use_k0,
-                  bool neutralize, const gps_opts* o, cudaStream_t st) {
-  PcgScalars* sc = P->sc;
-  const bool periodic = P->bc == GPS_BC_PERIODIC;
-  const size_t prof_from = t_prof ? t_prof->pending.size() : 0;
-  double* bg_sum = nullptr;
-  if (neutralize) {
-    launch_sum(rho, P->n, P->partials, &sc->counter[CNT_AUX], &sc->aux[3], st);
-    bg_sum = &sc->aux[3];
-  }
-  launch_init(rho, P->r, phi, P->p, P->Ap, P->n, o->tol_abs, o->tol_rel, o->max_iter, P->partials, sc,
-              1, bg_sum, st);
-  read_scalars(P, st);
-  PcgResult res{GPS_OK, 0, 0, std::sqrt(P->sc_host->rr0), std::sqrt(P->sc_host->rr0),
-                P->sc_host->background};
-  const bool mixed = o->precision == GPS_MIXED;
-  if (mixed) ensure_w32(P);
-  const bool gauge = periodic && !use_k0;   // singular periodic operator: keep v on the gauge
-  bool use32 = false;
-  int chunk = 2;
-  while (!P->sc_host->done) {
-    for (int c = 0; c < chunk; ++c) {
-      if (use32)
-        vacuum_pipeline<float2>(P, P->r, P->s, P->table, k0, use_k0, P->v, P->s, P->r, true, st, gauge);
-      else
-        vacuum_pipeline<double2>(P, P->r, P->s, P->table, k0, use_k0, P->v, P->s, P->r, true, st, gauge);
-      timed(5, st, [&] {
-        launch_update_p(P->v, P->r, qlam, P->sq, P->s, P->p, P->Ap, P->n, periodic ? 1 : 0,
-                        gauge ? 1 : 0, P->partials, sc, st);
-      });
-      timed(6, st, [&] { launch_update_r(phi, P->r, P->p, P->Ap, P->n, P->partials, sc, st); });
-    }
-    const int before = P->sc_host->iter;
-    read_scalars(P, st);
-    if (!use32) res.fp64_iters += P->sc_host->iter - before;
-    if (mixed && !use32 && std::sqrt(P->sc_host->rr) <= o->mixed_switch * res.res0) use32 = true;
-    if (chunk < 8) chunk *= 2;
-  }
-  res.status = P->sc_host->status;
-  res.iters = P->sc_host->iter;
-  if (t_prof && t_prof->on) t_prof->trim_loop(prof_from, res.iters);
-  res.res = std::sqrt(P->sc_host->rr);
-  return res;
-}
-
-// Certificate of a result (FP64): ||g|| / ||phi|| with
-// g = M(rho - bg [+ rions] - qlam phi / 4pi) [+ <sqrt(eps) phi> s] - phi.
-// Uses P->p and P->Ap as scratch.
-double certify(Plan* P, const double* rho, double bg, const double* rions, const double* qlam,
-               const double* phi, double k0, int use_k0, cudaStream_t st) {
-  const bool periodic = P->bc == GPS_BC_PERIODIC;
-  launch_fp_source(rho, rions, qlam, phi, P->sq, P->p, P->n, bg, P->partials, P->sc, st);
-  vacuum_pipeline<double2>(P, P->p, P->s, P->table, k0, use_k0, P->Ap, P->s, nullptr, false, st);
-  read_scalars(P, st);
-  const double c = periodic ? P->sc_host->aux[5] / (double)P->n : 0.0;
-  launch_fp_residual(P->Ap, P->s, phi, P->n, c, P->partials, P->partials2, P->sc, st);
-  read_scalars(P, st);
-  const double nphi = std::sqrt(P->sc_host->aux[7]);
-  return nphi > 0 ? std::sqrt(P->sc_host->aux[6]) / nphi : std::sqrt(P->sc_host->aux[6]);
-}
-
 IonParams ion_params(const gps_electrolyte* el) {
   const double NA = 6.02214076e23, a0 = 5.29177210903e-11, kB = 3.1668115634556e-6;
   IonParams ip;
   std::memset(&ip, 0, sizeof(ip));
+  ip.exp_cap = 40.0;
+  ip.inv_eps0m1 = 1.0;
+  if (!el) return ip;
   ip.nspecies = el->nspecies;
   const double kt = kB * el->temperature;
   ip.inv_kt = 1.0 / kt;
   ip.inv_eps0m1 = 1.0 / (el->eps0 - 1.0);
-  ip.exp_cap = 40.0;
+  double l = 0.0;
   for (int s = 0; s < el->nspecies; ++s) {
     const double nb = el->c_molar[s] * 1000.0 * NA * a0 * a0 * a0;
     ip.zq[s] = el->z[s];
     ip.zn[s] = el->z[s] * nb;
     ip.z2n_kt[s] = (double)el->z[s] * el->z[s] * nb / kt;
+    l += ip.z2n_kt[s];
   }
+  ip.lambda0 = kFourPi * l;
   return ip;
 }
 
-double lambda0_of(const gps_electrolyte* el) {
-  const IonParams ip = ion_params(el);
-  double l = 0.0;
-  for (int s = 0; s < ip.nspecies; ++s) l += ip.z2n_kt[s];
-  return kFourPi * l;
+int validate_grid(const gps_grid* g) {
+  if (!g) return GPS_ERR_INVALID;
+  if (g->nx < 4 || g->ny < 4 || g->nz < 4) return GPS_ERR_INVALID;
+  if (!(g->hx > 0) || !(g->hy > 0) || !(g->hz > 0)) return GPS_ERR_INVALID;
+  if (g->bc < GPS_BC_FREE || g->bc > GPS_BC_SURFACE) return GPS_ERR_INVALID;
+  const bool fx = g->bc == GPS_BC_FREE, fz = g->bc != GPS_BC_PERIODIC;
+  const int Px = fx ? 2 * g->nx : g->nx, Py = fx ? 2 * g->ny : g->ny, Pz = fz ? 2 * g->nz : g->nz;
+  for (int P : {Px, Py, Pz})
+    if (P % 2 || P > kMaxLen || !factorable(P)) return GPS_ERR_INVALID;
+  if (g->bc == GPS_BC_FREE) {
+    const double R = std::sqrt(std::pow(g->nx * g->hx, 2) + std::pow(g->ny * g->hy, 2) +
+                               std::pow(g->nz * g->hz, 2));
+    if (4 * g->nx * g->hx < g->nx * g->hx + R || 4 * g->ny * g->hy < g->ny * g->hy + R ||
+        4 * g->nz * g->hz < g->nz * g->hz + R)
+      return GPS_ERR_INVALID;   // aspect ratio too large for the 4x oversampled kernel
+  }
+  return GPS_OK;
 }
 
 int validate_el(const gps_electrolyte* el) {
@@ -611,151 +174,1048 @@ int validate_el(const gps_electrolyte* el) {
   return GPS_OK;
 }
 
-double now_ms() {
-  using namespace std::chrono;
-  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+bool same_grid(const gps_grid& a, const gps_grid& b) {
+  return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.hx == b.hx && a.hy == b.hy &&
+         a.hz == b.hz && a.bc == b.bc;
 }
 
-void fill_report(gps_report* rep, const PcgResult& r, double t0) {
+// Device allocations released together.
+struct DevMem {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  template <typename T>
+  T* alloc(size_t count) {
+    void* p = nullptr;
+    const size_t b = count * sizeof(T);
+    if (cudaMalloc(&p, b) != cudaSuccess) {
+      cudaGetLastError();
+      throw std::bad_alloc();
+    }
+    ptrs.push_back(p);
+    bytes += b;
+    return static_cast<T*>(p);
+  }
+  ~DevMem() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+// ------------------------------------------------------------- profiling --
+
+// Opt-in per-kernel timing with CUDA events on the launching stream.  Each
+// timed launch gets a device flag that its first serving block sets; launches
+// that found no slot to serve (the PCG had already converged) are dropped.
+struct Profiler {
+  bool on = false;
+  int mask = 0;
+  struct Rec { int kind; cudaEvent_t a, b; int flag; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  int* flags = nullptr;              // device, kFlags entries
+  static constexpr int kFlags = 1 << 15;
+  int next_flag = 0;
+  long long launches[GPS_PROFILE_KINDS] = {0};
+  double ms[GPS_PROFILE_KINDS] = {0};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  int* flag_for(int* idx) {
+    if (!flags) {
+      if (cudaMalloc(&flags, sizeof(int) * kFlags) != cudaSuccess) return nullptr;
+      cudaMemset(flags, 0, sizeof(int) * kFlags);
+    }
+    if (next_flag >= kFlags) resolve();
+    *idx = next_flag++;
+    return flags + *idx;
+  }
+  void resolve() {
+    if (pending.empty()) return;
+    cudaEventSynchronize(pending.back().b);
+    std::vector<int> acted(next_flag, 0);
+    if (flags && next_flag > 0) {
+      cudaMemcpy(acted.data(), flags, sizeof(int) * next_flag, cudaMemcpyDeviceToHost);
+      cudaMemset(flags, 0, sizeof(int) * next_flag);
+    }
+    for (auto& r : pending) {
+      float t = 0.f;
+      const bool did = r.flag < 0 || acted[r.flag];
+      if (did && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+        launches[r.kind] += 1;
+        ms[r.kind] += t;
+      }
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+    next_flag = 0;
+  }
+  ~Profiler() {
+    for (auto& r : pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+    if (flags) cudaFree(flags);
+  }
+};
+
+thread_local Profiler* t_prof = nullptr;
+
+// Runs launch(b') with b' = b plus the acted flag of a new profiling record
+// when kernels of this kind are being timed.
+template <typename F>
+void timed(int kind, const Batch& b, cudaStream_t st, F&& launch) {
+  if (!t_prof || !t_prof->on || !(t_prof->mask & (1 << kind))) {
+    launch(b);
+    return;
+  }
+  Batch bb = b;
+  int idx = -1;
+  bb.acted = t_prof->flag_for(&idx);
+  if (!bb.acted) idx = -1;
+  cudaEvent_t e0 = t_prof->get(), e1 = t_prof->get();
+  cudaEventRecord(e0, st);
+  launch(bb);
+  cudaEventRecord(e1, st);
+  t_prof->pending.push_back({kind, e0, e1, idx});
+}
+
+// ----------------------------------------------------------------- shapes --
+
+struct Shape {
+  gps_grid grid;
+  size_t n = 0;
+  int Px = 0, Py = 0, Pz = 0, Hx = 0;
+  int periodic = 0;
+  double inv_p = 0.0;
+  PassGeom g;                 // heuristic geometry (reduction sizing)
+  FftSched fx, fy, fz;
+  struct Sched {
+    bool tuned = false;
+    PassGeom g;
+    FftSched fx, fy, fz;
+  } sp[3];                    // per spectrum precision (Spec), set by the autotuner
+  double2 *twx64 = nullptr, *twy64 = nullptr, *twz64 = nullptr;
+  float2 *twx32 = nullptr, *twy32 = nullptr, *twz32 = nullptr;
+  dfc *twxdf = nullptr, *twydf = nullptr, *twzdf = nullptr;
+  double* table = nullptr;
+  double* lap = nullptr;
+  DevMem mem;
+};
+
+int batch_lines(int L, int units) {
+  int b = 2048 / L;
+  if (b < 1) b = 1;
+  const int want = units / 304;   // keep >= ~2 CTAs per SM
+  if (want < b) b = want < 1 ? 1 : want;
+  return b;
+}
+
+void upload_twiddles(Shape* S, int L, double2** t64, float2** t32, dfc** tdf) {
+  std::vector<double2> h64(L);
+  std::vector<float2> h32(L);
+  std::vector<dfc> hdf(L);
+  for (int m = 0; m < L; ++m) {
+    const long double ang = 2.0L * 3.141592653589793238462643383279502884L * m / L;
+    const long double c = cosl(ang), s = -sinl(ang);
+    h64[m].x = (double)c;
+    h64[m].y = (double)s;
+    h32[m].x = (float)h64[m].x;
+    h32[m].y = (float)h64[m].y;
+    // double-float split taken from the long double value
+    const float cx = (float)c, sy = (float)s;
+    hdf[m].x = df(cx, (float)(c - (long double)cx));
+    hdf[m].y = df(sy, (float)(s - (long double)sy));
+  }
+  *t64 = S->mem.alloc<double2>(L);
+  *t32 = S->mem.alloc<float2>(L);
+  *tdf = S->mem.alloc<dfc>(L);
+  ck(cudaMemcpy(*t64, h64.data(), L * sizeof(double2), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(*t32, h32.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(*tdf, hdf.data(), L * sizeof(dfc), cudaMemcpyHostToDevice));
+}
+
+// Free-BC table: h^3 g on the octant from the 4x oversampled truncated-Coulomb
+// transform (three even transforms), then its 2n-periodic transform (three
+// more), normalized by 1/(Px Py Pz).
+void build_free_table(Shape* S, cudaStream_t st) {
+  const int nx = S->grid.nx, ny = S->grid.ny, nz = S->grid.nz;
+  const double hx = S->grid.hx, hy = S->grid.hy, hz = S->grid.hz;
+  const int Mx = 4 * nx, My = 4 * ny, Mz = 4 * nz;
+  const int mx = Mx / 2 + 1, my = My / 2 + 1, mz = Mz / 2 + 1;
+  const double R = std::sqrt(std::pow(nx * hx, 2) + std::pow(ny * hy, 2) + std::pow(nz * hz, 2));
+  const int hxo = nx + 1, hyo = ny + 1, hzo = nz + 1;
+  DevMem tmp;
+  auto up = [&](const std::vector<double>& h) {
+    double* d = tmp.alloc<double>(h.size());
+    ck(cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return d;
+  };
+  double* ghat = tmp.alloc<double>((size_t)mx * my * mz);
+  launch_free_ghat(ghat, mx, my, mz, 2 * kPi / (Mx * hx), 2 * kPi / (My * hy), 2 * kPi / (Mz * hz), R, st);
+  double* cx = up(cosine_matrix(Mx, hxo, 1.0 / Mx));
+  double* cy = up(cosine_matrix(My, hyo, 1.0 / My));
+  double* cz = up(cosine_matrix(Mz, hzo, 1.0 / Mz));
+  double* t1 = tmp.alloc<double>((size_t)mz * my * hxo);
+  launch_axis_matrix(ghat, t1, cx, mz * my, mx, 1, hxo, st);
+  double* t2 = tmp.alloc<double>((size_t)mz * hyo * hxo);
+  launch_axis_matrix(t1, t2, cy, mz, my, hxo, hyo, st);
+  double* g = tmp.alloc<double>((size_t)hzo * hyo * hxo);
+  launch_axis_matrix(t2, g, cz, 1, mz, hyo * hxo, hzo, st);
+  // transform of the 2n-periodic even extension: M = 2n, entries m = 0..n
+  double* dx = up(cosine_matrix(2 * nx, hxo, 1.0 / (2 * nx)));
+  double* dy = up(cosine_matrix(2 * ny, hyo, 1.0 / (2 * ny)));
+  double* dz = up(cosine_matrix(2 * nz, hzo, 1.0 / (2 * nz)));
+  double* u1 = tmp.alloc<double>((size_t)hzo * hyo * hxo);
+  double* u2 = tmp.alloc<double>((size_t)hzo * hyo * hxo);
+  launch_axis_matrix(g, u1, dx, hzo * hyo, hxo, 1, hxo, st);
+  launch_axis_matrix(u1, u2, dy, hzo, hyo, hxo, hyo, st);
+  launch_axis_matrix(u2, S->table, dz, 1, hzo, hyo * hxo, hzo, st);
+  ck(cudaStreamSynchronize(st));
+  ck(cudaGetLastError());
+}
+
+std::shared_ptr<Shape> build_shape(const gps_grid* gr, cudaStream_t st) {
+  auto S = std::make_shared<Shape>();
+  S->grid = *gr;
+  const bool fx = gr->bc == GPS_BC_FREE, fz = gr->bc != GPS_BC_PERIODIC;
+  S->Px = fx ? 2 * gr->nx : gr->nx;
+  S->Py = fx ? 2 * gr->ny : gr->ny;
+  S->Pz = fz ? 2 * gr->nz : gr->nz;
+  S->Hx = S->Px / 2 + 1;
+  S->n = (size_t)gr->nx * gr->ny * gr->nz;
+  S->periodic = gr->bc == GPS_BC_PERIODIC;
+  S->inv_p = 1.0 / ((double)S->Px * S->Py * S->Pz);
+  PassGeom& g = S->g;
+  g.nx = gr->nx; g.ny = gr->ny; g.nz = gr->nz;
+  g.Px = S->Px; g.Py = S->Py; g.Pz = S->Pz; g.Hx = S->Hx;
+  g.nrows = gr->ny * gr->nz;
+  g.lines_x = batch_lines(S->Px, (g.nrows + 1) / 2);
+  g.tile_y = batch_lines(S->Py, S->Hx * gr->nz);
+  g.tile_z = batch_lines(S->Pz, S->Hx * S->Py);
+  if (!make_sched(S->Px, &S->fx) || !make_sched(S->Py, &S->fy) || !make_sched(S->Pz, &S->fz))
+    throw std::bad_alloc();
+  for (auto& sp : S->sp) {
+    sp.g = S->g;
+    sp.fx = S->fx;
+    sp.fy = S->fy;
+    sp.fz = S->fz;
+  }
+  upload_twiddles(S.get(), S->Px, &S->twx64, &S->twx32, &S->twxdf);
+  upload_twiddles(S.get(), S->Py, &S->twy64, &S->twy32, &S->twydf);
+  upload_twiddles(S.get(), S->Pz, &S->twz64, &S->twz32, &S->twzdf);
+  const int hy = S->Py / 2 + 1, hz = S->Pz / 2 + 1;
+  const size_t tab = (size_t)S->Hx * hy * hz;
+  S->table = S->mem.alloc<double>(tab);
+  const double dkx = 2 * kPi / (S->Px * gr->hx), dky = 2 * kPi / (S->Py * gr->hy),
+               dkz = 2 * kPi / (S->Pz * gr->hz);
+  if (gr->bc == GPS_BC_PERIODIC) {
+    S->lap = S->mem.alloc<double>(tab);
+    launch_table_periodic(S->table, S->lap, S->Hx, hy, hz, dkx, dky, dkz, S->inv_p, st);
+  } else if (gr->bc == GPS_BC_SURFACE) {
+    launch_table_surface(S->table, S->Hx, hy, hz, dkx, dky, dkz, gr->nz * gr->hz, S->inv_p, st);
+  } else {
+    build_free_table(S.get(), st);
+  }
+  ck(cudaStreamSynchronize(st));
+  ck(cudaGetLastError());
+  return S;
+}
+
+// ------------------------------------------------------------------ pools --
+
+}  // namespace
+
+struct Request {
+  gps_request req;
+  unsigned long long ticket = 0;
+  double t0 = 0.0;
+  bool done = false;
+  int status = GPS_PENDING;
+  gps_report rep{};
+};
+
+namespace {
+
+struct Pool {
+  std::shared_ptr<Shape> shape;
+  int cap = 1;
+  size_t n = 0, wn = 0;
+  int pstride = 0;
+  Fields f{};
+  double *own_rho = nullptr, *own_eps = nullptr, *own_phi = nullptr;
+  double2* W64 = nullptr;
+  float2* W32 = nullptr;
+  double *partials = nullptr, *partials2 = nullptr, *partials3 = nullptr;
+  SlotState* st = nullptr;
+  SlotState* st_host = nullptr;
+  int* active = nullptr;
+  int* active_host = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool has_nlpb = false, has_mixed = false, has_cert = false, has_fp64 = false, has_df64 = false;
+  std::vector<Request*> slot_req;
+  std::map<int, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
+  unsigned long long last_use = 0;
+  DevMem mem;
+
+  ~Pool() {
+    for (auto& kv : graphs) {
+      cudaGraphExecDestroy(kv.second.second);
+      cudaGraphDestroy(kv.second.first);
+    }
+    if (st_host) cudaFreeHost(st_host);
+    if (active_host) cudaFreeHost(active_host);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+  int busy() const {
+    int b = 0;
+    for (auto* r : slot_req) b += r != nullptr;
+    return b;
+  }
+};
+
+size_t slot_bytes(const Shape& S) {
+  const size_t wn = (size_t)S.Hx * S.Py * S.grid.nz;
+  return 18 * S.n * sizeof(double) + wn * (sizeof(double2) + sizeof(float2)) + 3 * 4096 * sizeof(double);
+}
+
+std::unique_ptr<Pool> make_pool(std::shared_ptr<Shape> shape, int cap, bool own_stream) {
+  auto P = std::make_unique<Pool>();
+  P->shape = shape;
+  P->cap = cap;
+  P->n = shape->n;
+  P->wn = (size_t)shape->Hx * shape->Py * shape->grid.nz;
+  P->pstride = std::max((shape->g.nrows + 1) / 2, vec_blocks(shape->n, cap)) + 32;
+  const size_t N = P->n * cap;
+  Fields& f = P->f;
+  P->own_rho = f.rho = P->mem.alloc<double>(N);
+  P->own_eps = f.eps = P->mem.alloc<double>(N);
+  P->own_phi = f.phi = P->mem.alloc<double>(N);
+  f.s = P->mem.alloc<double>(N);
+  f.sq = P->mem.alloc<double>(N);
+  f.q = P->mem.alloc<double>(N);
+  f.qlam = P->mem.alloc<double>(N);
+  f.r = P->mem.alloc<double>(N);
+  f.p = P->mem.alloc<double>(N);
+  f.Ap = P->mem.alloc<double>(N);
+  f.v = P->mem.alloc<double>(N);
+  f.rions = P->mem.alloc<double>(N);
+  f.rp = P->mem.alloc<double>(N);
+  f.fresh = P->mem.alloc<double>(N);
+  f.lam = P->mem.alloc<double>(N);
+  f.dphi = P->mem.alloc<double>(N);
+  f.src = P->mem.alloc<double>(N);
+  f.tmp = P->mem.alloc<double>(N);
+  P->W64 = P->mem.alloc<double2>(P->wn * cap);
+  P->W32 = P->mem.alloc<float2>(P->wn * cap);
+  P->partials = P->mem.alloc<double>((size_t)P->pstride * cap);
+  P->partials2 = P->mem.alloc<double>((size_t)P->pstride * cap);
+  P->partials3 = P->mem.alloc<double>((size_t)P->pstride * cap);
+  P->st = P->mem.alloc<SlotState>(cap);
+  P->active = P->mem.alloc<int>(cap + 1);
+  ck(cudaMemset(P->st, 0, sizeof(SlotState) * cap));
+  ck(cudaMemset(P->active, 0, sizeof(int) * (cap + 1)));
+  ck(cudaMallocHost((void**)&P->st_host, sizeof(SlotState) * cap));
+  ck(cudaMallocHost((void**)&P->active_host, sizeof(int) * (cap + 1)));
+  std::memset(P->st_host, 0, sizeof(SlotState) * cap);
+  std::memset(P->active_host, 0, sizeof(int) * (cap + 1));
+  P->slot_req.assign(cap, nullptr);
+  if (own_stream) {
+    ck(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+    P->own_stream = true;
+  }
+  return P;
+}
+
+Batch batch_of(Pool& P, int phase, int prec) {
+  Batch b;
+  b.active = P.active;
+  b.st = P.st;
+  b.phase = phase;
+  b.prec = prec;
+  b.vstride = P.n;
+  b.partials = P.partials;
+  b.partials2 = P.partials2;
+  b.partials3 = P.partials3;
+  b.pstride = P.pstride;
+  b.acted = nullptr;
+  return b;
+}
+
+template <typename V> constexpr int spec_of() {
+  return std::is_same<V, double2>::value ? SPEC_FP64 : std::is_same<V, float2>::value ? SPEC_FP32 : SPEC_DF64;
+}
+
+// One spectrum pipeline (five passes) for the slots of `b`.
+template <typename V>
+void pipeline(Pool& P, const Batch& b, PipeArgs a, cudaStream_t st) {
+  const Shape& S = *P.shape;
+  const V *twx, *twy, *twz;
+  if constexpr (std::is_same<V, double2>::value) {
+    twx = reinterpret_cast<const V*>(S.twx64);
+    twy = reinterpret_cast<const V*>(S.twy64);
+    twz = reinterpret_cast<const V*>(S.twz64);
+    a.W = P.W64;
+  } else if constexpr (std::is_same<V, dfc>::value) {
+    twx = S.twxdf;
+    twy = S.twydf;
+    twz = S.twzdf;
+    a.W = P.W64;   // same 16 bytes per complex; a slot uses one of the two at a time
+  } else {
+    twx = reinterpret_cast<const V*>(S.twx32);
+    twy = reinterpret_cast<const V*>(S.twy32);
+    twz = reinterpret_cast<const V*>(S.twz32);
+    a.W = P.W32;
+  }
+  a.wstride = P.wn;
+  const int ns = P.cap;
+  const Shape::Sched& sc = S.sp[spec_of<V>()];
+  timed(0, b, st, [&](const Batch& bb) { launch_x_fwd<V>(sc.g, sc.fx, twx, bb, a, ns, st); });
+  timed(1, b, st, [&](const Batch& bb) { launch_y<V>(sc.g, sc.fy, twy, bb, a, false, ns, st); });
+  timed(2, b, st, [&](const Batch& bb) { launch_z<V>(sc.g, sc.fz, twz, bb, a, ns, st); });
+  timed(3, b, st, [&](const Batch& bb) { launch_y<V>(sc.g, sc.fy, twy, bb, a, true, ns, st); });
+  timed(4, b, st, [&](const Batch& bb) { launch_x_inv<V>(sc.g, sc.fx, twx, bb, a, ns, st); });
+}
+
+// ------------------------------------------------------------- autotuner --
+//
+// For every grid and spectrum precision the lines per CTA of the x passes,
+// the columns per CTA of the y and z passes and the radix order of each axis
+// are chosen by timing the passes on the device (1 warm-up + 3 timed
+// launches each, fastest kept).  Results are cached for the process, keyed by
+// grid and precision, so every solve of a grid -- alone or batched -- uses
+// the same schedule (and therefore the same rounding).
+
+struct TuneKey {
+  int nx, ny, nz, bc, spec;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(nx, ny, nz, bc, spec) < std::tie(o.nx, o.ny, o.nz, o.bc, o.spec);
+  }
+};
+struct TuneVal {
+  PassGeom g;
+  FftSched fx, fy, fz;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+template <typename F>
+float time_launch(F&& launch, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  launch();
+  float best = 1e30f;
+  for (int r = 0; r < 3; ++r) {
+    cudaEventRecord(e0, st);
+    launch();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    best = std::min(best, t);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ck(cudaGetLastError());
+  return best;
+}
+
+std::vector<int> batch_candidates(int b0, int L, size_t vbytes) {
+  std::vector<int> c;
+  for (int b : {b0 / 2, b0, 2 * b0, 4 * b0}) {
+    if (b < 1 || b > 64) continue;
+    if (x_lines_smem_bytes(L, b, vbytes) > 220 * 1024) continue;
+    if (std::find(c.begin(), c.end(), b) == c.end()) c.push_back(b);
+  }
+  if (c.empty()) c.push_back(1);
+  return c;
+}
+
+template <typename V>
+void tune_spec(Shape& S, cudaStream_t st) {
+  constexpr int sp = spec_of<V>();
+  Shape::Sched& out = S.sp[sp];
+  if (out.tuned) return;
+  const TuneKey key{S.grid.nx, S.grid.ny, S.grid.nz, S.grid.bc, sp};
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto hit = g_tune.find(key);
+  if (hit == g_tune.end()) {
+    const V *twx, *twy, *twz;
+    if constexpr (std::is_same<V, double2>::value) {
+      twx = reinterpret_cast<const V*>(S.twx64);
+      twy = reinterpret_cast<const V*>(S.twy64);
+      twz = reinterpret_cast<const V*>(S.twz64);
+    } else if constexpr (std::is_same<V, dfc>::value) {
+      twx = S.twxdf;
+      twy = S.twydf;
+      twz = S.twzdf;
+    } else {
+      twx = reinterpret_cast<const V*>(S.twx32);
+      twy = reinterpret_cast<const V*>(S.twy32);
+      twz = reinterpret_cast<const V*>(S.twz32);
+    }
+    DevMem tmp;
+    const size_t wn = (size_t)S.Hx * S.Py * S.grid.nz;
+    V* W = tmp.alloc<V>(wn);
+    double* in = tmp.alloc<double>(S.n);
+    double* outv = tmp.alloc<double>(S.n);
+    ck(cudaMemsetAsync(in, 0, S.n * sizeof(double), st));
+    ck(cudaMemsetAsync(W, 0, wn * sizeof(V), st));
+    Batch b{};
+    PipeArgs a{};
+    a.in = in;
+    a.out = outv;
+    a.table = S.table;
+    a.W = W;
+    TuneVal best;
+    best.g = S.g;
+    best.fx = S.fx;
+    best.fy = S.fy;
+    best.fz = S.fz;
+    // x passes: lines per CTA and radix order of Px
+    float tbest = 1e30f;
+    for (int lines : batch_candidates(S.g.lines_x, S.Px, sizeof(V)))
+      for (int order = 0; order < 3; ++order) {
+        PassGeom g = best.g;
+        g.lines_x = lines;
+        FftSched fx;
+        if (!make_sched(S.Px, &fx, order)) continue;
+        const float t = time_launch([&] { launch_x_fwd<V>(g, fx, twx, b, a, 1, st); }, st) +
+                        time_launch([&] { launch_x_inv<V>(g, fx, twx, b, a, 1, st); }, st);
+        if (t < tbest) { tbest = t; best.g.lines_x = lines; best.fx = fx; }
+      }
+    tbest = 1e30f;
+    for (int tile : batch_candidates(S.g.tile_y, S.Py, sizeof(V)))
+      for (int order = 0; order < 3; ++order) {
+        PassGeom g = best.g;
+        g.tile_y = tile;
+        FftSched fy;
+        if (!make_sched(S.Py, &fy, order)) continue;
+        const float t = time_launch([&] { launch_y<V>(g, fy, twy, b, a, false, 1, st); }, st) +
+                        time_launch([&] { launch_y<V>(g, fy, twy, b, a, true, 1, st); }, st);
+        if (t < tbest) { tbest = t; best.g.tile_y = tile; best.fy = fy; }
+      }
+    tbest = 1e30f;
+    for (int tile : batch_candidates(S.g.tile_z, S.Pz, sizeof(V)))
+      for (int order = 0; order < 3; ++order) {
+        PassGeom g = best.g;
+        g.tile_z = tile;
+        FftSched fz;
+        if (!make_sched(S.Pz, &fz, order)) continue;
+        const float t = time_launch([&] { launch_z<V>(g, fz, twz, b, a, 1, st); }, st);
+        if (t < tbest) { tbest = t; best.g.tile_z = tile; best.fz = fz; }
+      }
+    ck(cudaStreamSynchronize(st));
+    hit = g_tune.emplace(key, best).first;
+  }
+  out.g = hit->second.g;
+  out.fx = hit->second.fx;
+  out.fy = hit->second.fy;
+  out.fz = hit->second.fz;
+  out.tuned = true;
+}
+
+// Tune the spectrum precisions a launch sequence may use (FP64 is always
+// needed: setup of periodic q and the certificate run in FP64).  Must run
+// outside stream capture.
+void ensure_tuned(Shape& S, bool fp32, bool df64, cudaStream_t st) {
+  tune_spec<double2>(S, st);
+  if (fp32) tune_spec<float2>(S, st);
+  if (df64) tune_spec<dfc>(S, st);
+}
+
+void launch_setup_group(Pool& P, cudaStream_t st) {
+  const Shape& S = *P.shape;
+  const Batch b = batch_of(P, PH_SETUP, -1);
+  timed(7, b, st, [&](const Batch& bb) { launch_setup_s(bb, P.f, P.n, P.cap, st); });
+  if (S.periodic) {
+    PipeArgs a{};
+    a.in = P.f.sq;
+    a.out = P.f.q;
+    a.out_scale = P.f.sq;
+    a.table = S.lap;
+    pipeline<double2>(P, b, a, st);
+  } else {
+    const int per_xy = S.grid.bc == GPS_BC_SURFACE ? 1 : 0;   // surface: x, y wrap; z free
+    launch_fd16_q(b, P.f, S.grid.nx, S.grid.ny, S.grid.nz, S.grid.hx, S.grid.hy, S.grid.hz, per_xy,
+                  per_xy, 0, fd16_coeffs(), P.cap, st);
+  }
+}
+
+// One round: every stage of the phase machine once and `m` PCG iterations.
+void launch_round(Pool& P, int m, bool setup, bool init, cudaStream_t st) {
+  const Shape& S = *P.shape;
+  const size_t n = P.n;
+  const int ns = P.cap;
+  const Fields& f = P.f;
+  const int periodic = S.periodic;
+  if (setup) {
+    launch_setup_group(P, st);
+    launch_setup_final(batch_of(P, PH_SETUP, -1), f, n, S.inv_p, periodic, ns, st);
+  }
+  if (P.has_nlpb) launch_nl_eval(batch_of(P, PH_NLEVAL, -1), f, n, S.inv_p, periodic, ns, st);
+  if (init || P.has_nlpb) launch_init(batch_of(P, PH_INIT, -1), f, n, ns, st);
+  PipeArgs it{};
+  it.in = f.r;
+  it.in_scale = f.s;
+  it.out = f.v;
+  it.out_scale = f.s;
+  it.dot_with = f.r;
+  it.table = S.table;
+  it.slot_k0 = 1;
+  it.red_mu = periodic;
+  it.red_wsum = periodic;
+  const Batch bi64 = batch_of(P, PH_ITER, SPEC_FP64), bi32 = batch_of(P, PH_ITER, SPEC_FP32);
+  const Batch bidf = batch_of(P, PH_ITER, SPEC_DF64);
+  const Batch bi = batch_of(P, PH_ITER, -1);
+  for (int i = 0; i < m; ++i) {
+    if (P.has_fp64) pipeline<double2>(P, bi64, it, st);
+    if (P.has_df64) pipeline<dfc>(P, bidf, it, st);
+    if (P.has_mixed) pipeline<float2>(P, bi32, it, st);
+    timed(5, bi, st, [&](const Batch& bb) { launch_update_p(bb, f, n, periodic, ns, st); });
+    timed(6, bi, st, [&](const Batch& bb) { launch_update_r(bb, f, n, ns, st); });
+  }
+  if (P.has_nlpb) {
+    launch_nl_step(batch_of(P, PH_TRIAL, -1), f, n, 0, ns, st);
+    launch_nl_step(batch_of(P, PH_COMMIT, -1), f, n, 1, ns, st);
+  }
+  if (P.has_cert) {
+    const Batch bc = batch_of(P, PH_CERT, -1);
+    launch_fp_source(bc, f, n, ns, st);
+    PipeArgs c{};
+    c.in = f.tmp;
+    c.in_scale = f.s;
+    c.out = f.Ap;
+    c.out_scale = f.s;
+    c.table = S.table;
+    c.slot_k0 = 1;
+    pipeline<double2>(P, bc, c, st);
+    launch_fp_residual(bc, f, n, periodic, ns, st);
+  }
+}
+
+// The slot state of a new request.
+SlotState initial_state(int kind, const gps_electrolyte* el, const gps_opts& o) {
+  SlotState s;
+  std::memset(&s, 0, sizeof(s));
+  s.ion = ion_params(kind == GPS_GPE ? nullptr : el);
+  s.phase = PH_SETUP;
+  s.kind = kind;
+  s.status = GPS_OK;
+  s.tol_abs = o.tol_abs;
+  s.tol_rel = o.tol_rel;
+  s.max_iter = o.max_iter > 0 ? o.max_iter : 1;
+  const bool df = o.precision == GPS_DF64 || o.precision == GPS_MIXED_DF64;
+  s.spec_hi = df ? SPEC_DF64 : SPEC_FP64;
+  s.spec = s.spec_hi;
+  s.mixed = (o.precision == GPS_MIXED || o.precision == GPS_MIXED_DF64) ? 1 : 0;
+  s.mixed_switch = o.mixed_switch;
+  s.certify = (o.certify || s.mixed) ? 1 : 0;
+  s.newton = o.outer_mode == GPS_OUTER_NEWTON ? 1 : 0;
+  s.eta = o.eta;
+  s.forcing = o.forcing;
+  s.tol_outer = o.tol_outer;
+  s.max_outer = o.max_outer;
+  s.neutralize = kind == GPS_GPE ? 1 : 0;
+  s.cert = -1.0;
+  s.F0 = -1.0;
+  return s;
+}
+
+void fill_report(gps_report* rep, const SlotState& s, double t0) {
   if (!rep) return;
-  rep->status = r.status;
-  rep->iters = r.iters;
-  rep->fp64_iters = r.fp64_iters;
-  rep->res0 = r.res0;
-  rep->res = r.res;
-  rep->background = r.background;
-  rep->fixed_point_res = -1.0;
+  std::memset(rep, 0, sizeof(*rep));
+  rep->status = s.status;
+  rep->iters = s.iters_total;
+  rep->outer_iters = s.outer;
+  rep->fp64_iters = s.fp64_iters;
+  rep->res0 = std::sqrt(s.rr0);
+  rep->res = std::sqrt(s.rr);
+  rep->outer_res = s.F;
+  rep->background = s.background;
+  rep->fixed_point_res = s.cert;
   rep->time_ms = now_ms() - t0;
 }
 
-// Core solve on device pointers (shared by the device and host entry points).
-int solve_core(gps_ctx* ctx, const gps_grid* gr, const double* rho, const double* eps,
-               const gps_electrolyte* el, int kind, double* phi, const gps_opts* oin,
-               gps_report* rep, cudaStream_t st, double t0, Plan* P) {
-  gps_opts o;
-  if (oin) o = *oin; else gps_default_opts(&o);
-  if (rep) std::memset(rep, 0, sizeof(*rep));
-  if (kind != GPS_GPE) {
-    int e = validate_el(el);
-    if (e != GPS_OK) return e;
+void put_state(Pool& P, int slot, const SlotState& s, cudaStream_t st) {
+  P.st_host[slot] = s;
+  ck(cudaMemcpyAsync(P.st + slot, P.st_host + slot, sizeof(SlotState), cudaMemcpyHostToDevice, st));
+}
+
+void put_active(Pool& P, cudaStream_t st) {
+  int c = 0;
+  for (int k = 0; k < P.cap; ++k)
+    if (P.slot_req[k]) P.active_host[1 + c++] = k;
+  P.active_host[0] = c;
+  ck(cudaMemcpyAsync(P.active, P.active_host, sizeof(int) * (P.cap + 1), cudaMemcpyHostToDevice, st));
+}
+
+void get_states(Pool& P, cudaStream_t st) {
+  ck(cudaMemcpyAsync(P.st_host, P.st, sizeof(SlotState) * P.cap, cudaMemcpyDeviceToHost, st));
+}
+
+// Engine: continuous batching over pools of one device.
+struct Engine {
+  int device = 0;
+  size_t budget = 0;
+  int max_slots = 0;
+  std::vector<std::shared_ptr<Shape>> shapes;
+  std::vector<std::unique_ptr<Pool>> pools;
+  std::deque<Request*> queue;
+  unsigned long long clock = 0;
+  int max_concurrent = 0;
+  bool use_graphs = true;
+
+  size_t bytes() const {
+    size_t b = 0;
+    for (auto& s : shapes) b += s->mem.bytes;
+    for (auto& p : pools) b += p->mem.bytes;
+    return b;
   }
-  setup_fields(P, eps, st);
-  read_scalars(P, st);
-  if (P->sc_host->bad_eps) {
-    P->sc_host->bad_eps = 0;
-    ck(cudaMemsetAsync(&P->sc->bad_eps, 0, sizeof(int), st));
-    return GPS_ERR_INVALID;
+
+  int capacity_for(const Shape& S) const {
+    int c = (int)std::lround(4.0e6 / (double)S.n);
+    c = std::max(2, std::min(16, c));
+    if (max_slots > 0) c = std::min(c, max_slots);
+    return c;
   }
-  const bool periodic = P->bc == GPS_BC_PERIODIC;
-  const double N = (double)P->n;
-  const double invN = 1.0 / ((double)P->Px * P->Py * P->Pz);
-  const bool want_cert = o.certify || o.precision == GPS_MIXED;
-  if (kind == GPS_GPE) {
-    PcgResult r = run_pcg(P, rho, phi, P->q, 0.0, 0, periodic, &o, st);
-    fill_report(rep, r, t0);
-    if (rep && want_cert && r.status == GPS_OK)
-      rep->fixed_point_res = certify(P, rho, r.background, nullptr, P->q, phi, 0.0, 0, st);
-    return r.status;
-  }
-  const double lam0 = lambda0_of(el);
-  const IonParams ip = ion_params(el);
-  double eps_mean = 0.0;
-  if (periodic) {
-    launch_sum(eps, P->n, P->partials, &P->sc->counter[CNT_AUX], &P->sc->aux[4], st);
-    read_scalars(P, st);
-    eps_mean = P->sc_host->aux[4] / N;
-  }
-  if (kind == GPS_LPB) {
-    launch_qlam_linear(P->q, eps, P->qlam, P->n, lam0, ip.inv_eps0m1, P->partials, P->sc, st);
-    read_scalars(P, st);
-    const double lam_mean = P->sc_host->aux[1] / N;
-    const bool k0 = periodic && lam_mean > 0;
-    const double k0v = k0 ? kFourPi * eps_mean / lam_mean * invN : 0.0;
-    PcgResult r = run_pcg(P, rho, phi, P->qlam, k0v, k0 ? 1 : 0, periodic && !k0, &o, st);
-    fill_report(rep, r, t0);
-    if (rep && want_cert && r.status == GPS_OK)
-      rep->fixed_point_res = certify(P, rho, r.background, nullptr, P->qlam, phi, k0v, k0 ? 1 : 0, st);
-    return r.status;
-  }
-  if (kind != GPS_NLPB) return GPS_ERR_INVALID;
-  // Algorithm 4 (see gps.h): bookkeeping A phi = -4 pi (rho + rions - rp).
-  try {
-    ensure_nl(P);
-  } catch (std::bad_alloc&) {
-    return GPS_ERR_NOMEM;
-  }
-  const bool newton = o.outer_mode == GPS_OUTER_NEWTON;
-  ck(cudaMemsetAsync(phi, 0, P->n * sizeof(double), st));
-  launch_ionic_charge(phi, eps, P->rions, P->n, ip, st);
-  ck(cudaMemcpyAsync(P->rp, rho, P->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  double F0 = -1.0, F = 0.0;
-  int outer = 0, total_iters = 0, status = GPS_ERR_NOT_CONVERGED, fp64_iters = 0;
-  PcgResult last{GPS_OK, 0, 0, 0, 0, 0};
-  for (; outer <= o.max_outer; ++outer) {
-    launch_nl_eval(phi, eps, P->rions, P->rp, P->fresh, P->lam, P->n, ip, newton ? 1 : 0,
-                   P->partials, P->sc, st);
-    read_scalars(P, st);
-    F = std::sqrt(P->sc_host->aux[0]);
-    if (F0 < 0) F0 = F;
-    if (!std::isfinite(F)) { status = GPS_ERR_BREAKDOWN; break; }
-    if (F <= o.tol_outer) { status = GPS_OK; break; }
-    if (outer == o.max_outer) break;
-    const double e = newton ? 1.0 : o.eta;
-    launch_nl_source(P->fresh, P->rions, P->rp, P->q, P->lam, P->src, P->qlam, P->n, e, P->partials,
-                     P->sc, st);
-    read_scalars(P, st);
-    const double lam_mean = P->sc_host->aux[1] / N;
-    const bool k0 = periodic && lam_mean > 0;
-    gps_opts io = o;
-    if (newton) {
-      io.tol_abs = 0.1 * kFourPi * o.tol_outer;
-      io.tol_rel = std::fmin(o.forcing, F / F0);
-    } else if (outer < 2) {
-      io.tol_abs = 0.0;
-      io.tol_rel = 1e-4;
-    } else {
-      io.tol_abs = kFourPi * o.tol_outer;
-      io.tol_rel = 0.0;
+
+  // Pool for a request's grid: an existing one with a free slot, or a new one
+  // if the budget allows (evicting idle pools first).  nullptr: not now.
+  Pool* pool_for(const gps_grid& g) {
+    for (auto& p : pools)
+      if (same_grid(p->shape->grid, g) && p->busy() < p->cap) return p.get();
+    for (auto& p : pools)
+      if (same_grid(p->shape->grid, g)) return nullptr;   // full: wait for a slot
+    std::shared_ptr<Shape> shape;
+    for (auto& s : shapes)
+      if (same_grid(s->grid, g)) shape = s;
+    if (!shape) {
+      shape = build_shape(&g, nullptr);
+      shapes.push_back(shape);
     }
-    last = run_pcg(P, P->src, P->dphi, P->qlam, k0 ? kFourPi * eps_mean / lam_mean * invN : 0.0,
-                   k0 ? 1 : 0, periodic && !k0, &io, st);
-    total_iters += last.iters;
-    fp64_iters += last.fp64_iters;
-    if (last.status == GPS_ERR_BREAKDOWN) { status = last.status; break; }
-    double t = 1.0;
-    if (newton) {
-      while (t > 1e-4) {
-        launch_nl_step(phi, eps, P->rions, P->rp, P->fresh, P->lam, P->dphi, P->r, P->n, ip, e, t, 0,
-                       P->partials, P->sc, st);
-        read_scalars(P, st);
-        if (std::sqrt(P->sc_host->aux[2]) < F) break;
-        t *= 0.5;
+    const int cap = capacity_for(*shape);
+    const size_t need = slot_bytes(*shape) * cap;
+    while (budget && bytes() + need > budget) {
+      int victim = -1;
+      bool any_busy = false;
+      for (size_t i = 0; i < pools.size(); ++i) {
+        any_busy |= pools[i]->busy() > 0;
+        if (pools[i]->busy() == 0 && (victim < 0 || pools[i]->last_use < pools[victim]->last_use))
+          victim = (int)i;
+      }
+      if (victim < 0) {
+        if (any_busy) return nullptr;   // memory frees when a busy pool drains: wait
+        throw std::bad_alloc();         // the request can never fit the budget
+      }
+      pools.erase(pools.begin() + victim);
+    }
+    pools.push_back(make_pool(shape, cap, true));
+    return pools.back().get();
+  }
+
+  void admit(Pool& P, Request* r) {
+    int k = 0;
+    while (P.slot_req[k]) ++k;
+    P.slot_req[k] = r;
+    const gps_request& q = r->req;
+    const size_t b = P.n * sizeof(double);
+    ck(cudaMemcpyAsync(P.f.rho + k * P.n, q.rho_host, b, cudaMemcpyHostToDevice, P.stream));
+    ck(cudaMemcpyAsync(P.f.eps + k * P.n, q.eps_host, b, cudaMemcpyHostToDevice, P.stream));
+    SlotState s = initial_state(q.kind, &q.el, q.opts);
+    put_state(P, k, s, P.stream);
+    P.has_nlpb |= q.kind == GPS_NLPB;
+    P.has_mixed |= s.mixed != 0;
+    P.has_cert |= s.certify != 0;
+    P.has_fp64 |= s.spec_hi == SPEC_FP64;
+    P.has_df64 |= s.spec_hi == SPEC_DF64;
+  }
+
+  void run_round(Pool& P) {
+    ensure_tuned(*P.shape, P.has_mixed, P.has_df64, P.stream);
+    put_active(P, P.stream);
+    const int m = 4;
+    const int key = (P.has_nlpb ? 1 : 0) | (P.has_mixed ? 2 : 0) | (P.has_cert ? 4 : 0) |
+                    (P.has_fp64 ? 8 : 0) | (P.has_df64 ? 16 : 0);
+    const bool graphs_ok = use_graphs && !(t_prof && t_prof->on);
+    if (graphs_ok) {
+      auto it = P.graphs.find(key);
+      if (it == P.graphs.end()) {
+        cudaGraph_t g;
+        cudaGraphExec_t ge;
+        ck(cudaStreamBeginCapture(P.stream, cudaStreamCaptureModeRelaxed));
+        launch_round(P, m, true, true, P.stream);
+        ck(cudaStreamEndCapture(P.stream, &g));
+        ck(cudaGraphInstantiate(&ge, g, 0));
+        it = P.graphs.emplace(key, std::make_pair(g, ge)).first;
+      }
+      ck(cudaGraphLaunch(it->second.second, P.stream));
+    } else {
+      launch_round(P, m, true, true, P.stream);
+    }
+    get_states(P, P.stream);
+  }
+
+  // Copy out and release the finished slots of P (after its stream synced).
+  int collect(Pool& P) {
+    int finished = 0;
+    for (int k = 0; k < P.cap; ++k) {
+      Request* r = P.slot_req[k];
+      if (!r) continue;
+      const SlotState s = P.st_host[k];
+      if (s.phase != PH_DONE) continue;
+      ck(cudaMemcpyAsync(r->req.phi_host, P.f.phi + k * P.n, P.n * sizeof(double),
+                         cudaMemcpyDeviceToHost, P.stream));
+      ck(cudaStreamSynchronize(P.stream));
+      fill_report(&r->rep, s, r->t0);
+      r->status = s.status;
+      r->done = true;
+      P.slot_req[k] = nullptr;
+      SlotState idle;
+      std::memset(&idle, 0, sizeof(idle));
+      put_state(P, k, idle, P.stream);
+      ++finished;
+    }
+    return finished;
+  }
+
+  // Admit what fits, advance every busy pool by one round, collect.
+  // Returns the number of requests still queued or in slots.
+  size_t step() {
+    for (auto it = queue.begin(); it != queue.end();) {
+      Request* r = *it;
+      int v = validate_grid(&r->req.grid);
+      if (v == GPS_OK && r->req.kind != GPS_GPE) v = validate_el(&r->req.el);
+      if (v == GPS_OK && (r->req.kind < GPS_GPE || r->req.kind > GPS_NLPB)) v = GPS_ERR_INVALID;
+      if (v == GPS_OK && (!r->req.rho_host || !r->req.eps_host || !r->req.phi_host)) v = GPS_ERR_INVALID;
+      if (v != GPS_OK) {
+        r->status = v;
+        r->rep.status = v;
+        r->done = true;
+        it = queue.erase(it);
+        continue;
+      }
+      Pool* P = nullptr;
+      try {
+        P = pool_for(r->req.grid);
+      } catch (std::bad_alloc&) {
+        P = nullptr;
+        bool any_busy = false;
+        for (auto& p : pools) any_busy |= p->busy() > 0;
+        if (!any_busy) {   // nothing will free memory: fail the request
+          r->status = GPS_ERR_NOMEM;
+          r->rep.status = GPS_ERR_NOMEM;
+          r->done = true;
+          it = queue.erase(it);
+          continue;
+        }
+      }
+      if (P) {
+        admit(*P, r);
+        it = queue.erase(it);
+      } else {
+        ++it;
       }
     }
-    launch_nl_step(phi, eps, P->rions, P->rp, P->fresh, P->lam, P->dphi, P->r, P->n, ip, e, t, 1,
-                   P->partials, P->sc, st);
+    int busy_total = 0;
+    for (auto& p : pools) busy_total += p->busy();
+    max_concurrent = std::max(max_concurrent, busy_total);
+    // one round on every busy pool, all streams in flight together
+    for (auto& p : pools)
+      if (p->busy()) {
+        p->last_use = ++clock;
+        run_round(*p);
+      }
+    for (auto& p : pools)
+      if (p->busy()) {
+        ck(cudaStreamSynchronize(p->stream));
+        collect(*p);
+      }
+    size_t left = queue.size();
+    for (auto& p : pools) left += p->busy();
+    return left;
   }
-  double cert = -1.0;
-  if (want_cert && status == GPS_OK) {
-    launch_ionic_charge(phi, eps, P->fresh, P->n, ip, st);
-    cert = certify(P, rho, 0.0, P->fresh, P->q, phi, 0.0, 0, st);
+};
+
+}  // namespace
+
+// ----------------------------------------------------------- the context --
+
+struct gps_ctx {
+  Profiler prof;
+  int device = 0;
+  size_t budget = 0;
+  std::vector<std::shared_ptr<Shape>> shapes;
+  std::vector<std::unique_ptr<Pool>> direct;   // one-slot pools of the single-solve path
+  unsigned long long clock = 0;
+  size_t in_use() const {
+    size_t b = 0;
+    for (auto& s : shapes) b += s->mem.bytes;
+    for (auto& p : direct) b += p->mem.bytes;
+    return b;
   }
-  ck(cudaStreamSynchronize(st));
-  if (rep) {
-    rep->fixed_point_res = cert;
-    rep->status = status;
-    rep->iters = total_iters;
-    rep->fp64_iters = fp64_iters;
-    rep->outer_iters = outer;
-    rep->res0 = last.res0;
-    rep->res = last.res;
-    rep->outer_res = F;
-    rep->time_ms = now_ms() - t0;
+};
+
+namespace {
+
+std::shared_ptr<Shape> get_shape(std::vector<std::shared_ptr<Shape>>& shapes, const gps_grid* gr,
+                                 cudaStream_t st) {
+  for (auto& s : shapes)
+    if (same_grid(s->grid, *gr)) return s;
+  auto s = build_shape(gr, st);
+  shapes.push_back(s);
+  return s;
+}
+
+// Single solve in the context's one-slot pool of this grid, on `st`.
+// rho/eps/phi are device pointers (the caller's, or the pool's own).
+int solve_direct(Pool& P, const double* rho, const double* eps, double* phi, int kind,
+                 const gps_electrolyte* el, const gps_opts& o, gps_report* rep, cudaStream_t st,
+                 double t0) {
+  P.f.rho = const_cast<double*>(rho);
+  P.f.eps = const_cast<double*>(eps);
+  P.f.phi = phi;
+  P.slot_req[0] = reinterpret_cast<Request*>(&P);   // marks slot 0 busy
+  SlotState s = initial_state(kind, el, o);
+  put_state(P, 0, s, st);
+  P.has_nlpb = kind == GPS_NLPB;
+  P.has_mixed = s.mixed != 0;
+  P.has_cert = s.certify != 0;
+  P.has_fp64 = s.spec_hi == SPEC_FP64;
+  P.has_df64 = s.spec_hi == SPEC_DF64;
+  put_active(P, st);
+  ensure_tuned(*P.shape, P.has_mixed, P.has_df64, st);
+  int m = 2;
+  bool first = true;
+  for (;;) {
+    launch_round(P, m, first, first || P.has_nlpb, st);
+    first = false;
+    get_states(P, st);
+    ck(cudaStreamSynchronize(st));
+    if (t_prof) t_prof->resolve();
+    if (P.st_host[0].phase == PH_DONE || P.st_host[0].phase == PH_IDLE) break;
+    if (m < 8) m *= 2;
   }
+  P.slot_req[0] = nullptr;
+  P.f.rho = P.own_rho;
+  P.f.eps = P.own_eps;
+  P.f.phi = P.own_phi;
+  fill_report(rep, P.st_host[0], t0);
+  return P.st_host[0].status;
+}
+
+Pool* direct_pool(gps_ctx* ctx, const gps_grid* gr, cudaStream_t st) {
+  ++ctx->clock;
+  for (auto& p : ctx->direct)
+    if (same_grid(p->shape->grid, *gr)) {
+      p->last_use = ctx->clock;
+      return p.get();
+    }
+  auto shape = get_shape(ctx->shapes, gr, st);
+  const size_t need = slot_bytes(*shape);
+  while (ctx->budget && ctx->in_use() + need > ctx->budget && !ctx->direct.empty()) {
+    size_t lru = 0;
+    for (size_t i = 1; i < ctx->direct.size(); ++i)
+      if (ctx->direct[i]->last_use < ctx->direct[lru]->last_use) lru = i;
+    auto victim_shape = ctx->direct[lru]->shape;
+    ctx->direct.erase(ctx->direct.begin() + lru);
+    for (size_t i = 0; i < ctx->shapes.size(); ++i)
+      if (ctx->shapes[i] == victim_shape && victim_shape != shape) {
+        ctx->shapes.erase(ctx->shapes.begin() + i);
+        break;
+      }
+  }
+  if (ctx->budget && ctx->in_use() + need > ctx->budget) throw std::bad_alloc();
+  ctx->direct.push_back(make_pool(shape, 1, false));
+  ctx->direct.back()->last_use = ctx->clock;
+  return ctx->direct.back().get();
+}
+
+struct ProfScope {
+  explicit ProfScope(gps_ctx* c) { t_prof = c ? &c->prof : nullptr; }
+  ~ProfScope() {
+    if (t_prof) t_prof->resolve();
+    t_prof = nullptr;
+  }
+};
+
+int finish(int status, cudaStream_t st) {
+  if (cudaStreamSynchronize(st) != cudaSuccess) return GPS_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return GPS_ERR_CUDA;
   return status;
 }
 
 }  // namespace
+
+// ------------------------------------------------------------- the server --
+
+struct gps_server {
+  Engine eng;
+  std::mutex mu;
+  std::condition_variable cv, done_cv;
+  std::deque<Request*> incoming;
+  std::map<unsigned long long, std::unique_ptr<Request>> reqs;
+  unsigned long long next_ticket = 1;
+  bool stop = false;
+  int fatal = GPS_OK;
+  std::thread worker;
+
+  size_t busy() const {
+    size_t b = eng.queue.size();
+    for (auto& p : eng.pools) b += p->busy();
+    return b;
+  }
+
+  void loop() {
+    cudaSetDevice(eng.device);
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return stop || !incoming.empty() || busy() > 0; });
+        if (stop) return;
+        while (!incoming.empty()) {
+          eng.queue.push_back(incoming.front());
+          incoming.pop_front();
+        }
+      }
+      bool failed = false;
+      size_t before = 0, after = 0;
+      try {
+        before = busy();
+        after = eng.step();
+      } catch (...) {
+        failed = true;
+      }
+      bool idle_pools = true;
+      for (auto& p : eng.pools) idle_pools &= p->busy() == 0;
+      if (!failed && after > 0 && after == before && idle_pools)
+        std::this_thread::sleep_for(std::chrono::milliseconds(1));   // queued work waiting for memory
+      std::lock_guard<std::mutex> lk(mu);
+      if (failed) {
+        fatal = GPS_ERR_CUDA;
+        for (auto& kv : reqs)
+          if (!kv.second->done) {
+            kv.second->status = GPS_ERR_CUDA;
+            kv.second->rep.status = GPS_ERR_CUDA;
+            kv.second->done = true;
+          }
+        eng.queue.clear();
+        done_cv.notify_all();
+        return;
+      }
+      done_cv.notify_all();
+    }
+  }
+};
 
 // ---------------------------------------------------------------- ABI ------
 
@@ -763,6 +1223,7 @@ extern "C" {
 
 void gps_default_opts(gps_opts* o) {
   if (!o) return;
+  std::memset(o, 0, sizeof(*o));
   o->tol_abs = 1e-10;
   o->tol_rel = 0.0;
   o->max_iter = 500;
@@ -814,44 +1275,35 @@ void gps_destroy(gps_ctx* c) {
 
 size_t gps_bytes_in_use(const gps_ctx* c) { return c ? c->in_use() : 0; }
 
-struct ProfScope {
-  explicit ProfScope(gps_ctx* c) { t_prof = c ? &c->prof : nullptr; }
-  ~ProfScope() {
-    if (t_prof) t_prof->resolve();
-    t_prof = nullptr;
-  }
-};
-
 #define GPS_GUARD_BEGIN try {
 #define GPS_GUARD_END                  \
   }                                    \
   catch (CudaError&) {                 \
+    cudaGetLastError();                \
     return GPS_ERR_CUDA;               \
   }                                    \
   catch (std::bad_alloc&) {            \
     return GPS_ERR_NOMEM;              \
   }
 
-static int finish(int status, cudaStream_t st) {
-  if (cudaStreamSynchronize(st) != cudaSuccess) return GPS_ERR_CUDA;
-  if (cudaGetLastError() != cudaSuccess) return GPS_ERR_CUDA;
-  return status;
-}
-
 int gps_pb_solve(gps_ctx* ctx, const gps_grid* grid, const double* rho, const double* eps,
                  const gps_electrolyte* el, int kind, double* phi, const gps_opts* opts,
                  gps_report* rep, void* stream) {
   const double t0 = now_ms();
+  if (rep) std::memset(rep, 0, sizeof(*rep));
   if (!ctx || !rho || !eps || !phi) return GPS_ERR_INVALID;
   if (kind < GPS_GPE || kind > GPS_NLPB) return GPS_ERR_INVALID;
+  int v = validate_grid(grid);
+  if (v != GPS_OK) return v;
+  if (kind != GPS_GPE && (v = validate_el(el)) != GPS_OK) return v;
+  gps_opts o;
+  if (opts) o = *opts; else gps_default_opts(&o);
   cudaStream_t st = (cudaStream_t)stream;
   GPS_GUARD_BEGIN
-  ProfScope prof_scope(ctx);
   cudaSetDevice(ctx->device);
-  Plan* P = nullptr;
-  int e = get_plan(ctx, grid, st, &P);
-  if (e != GPS_OK) return e;
-  int s = solve_core(ctx, grid, rho, eps, el, kind, phi, opts, rep, st, t0, P);
+  ProfScope prof_scope(ctx);
+  Pool* P = direct_pool(ctx, grid, st);
+  int s = solve_direct(*P, rho, eps, phi, kind, el, o, rep, st, t0);
   s = finish(s, st);
   if (rep) rep->time_ms = now_ms() - t0;
   return s;
@@ -867,21 +1319,24 @@ int gps_pb_solve_host(gps_ctx* ctx, const gps_grid* grid, const double* rho_h, c
                       const gps_electrolyte* el, int kind, double* phi_h, const gps_opts* opts,
                       gps_report* rep, void* stream) {
   const double t0 = now_ms();
+  if (rep) std::memset(rep, 0, sizeof(*rep));
   if (!ctx || !rho_h || !eps_h || !phi_h) return GPS_ERR_INVALID;
   if (kind < GPS_GPE || kind > GPS_NLPB) return GPS_ERR_INVALID;
+  int v = validate_grid(grid);
+  if (v != GPS_OK) return v;
+  if (kind != GPS_GPE && (v = validate_el(el)) != GPS_OK) return v;
+  gps_opts o;
+  if (opts) o = *opts; else gps_default_opts(&o);
   cudaStream_t st = (cudaStream_t)stream;
   GPS_GUARD_BEGIN
-  ProfScope prof_scope(ctx);
   cudaSetDevice(ctx->device);
-  Plan* P = nullptr;
-  int e = get_plan(ctx, grid, st, &P);
-  if (e != GPS_OK) return e;
-  ensure_io(P);
+  ProfScope prof_scope(ctx);
+  Pool* P = direct_pool(ctx, grid, st);
   const size_t b = P->n * sizeof(double);
-  ck(cudaMemcpyAsync(P->io_rho, rho_h, b, cudaMemcpyHostToDevice, st));
-  ck(cudaMemcpyAsync(P->io_eps, eps_h, b, cudaMemcpyHostToDevice, st));
-  int s = solve_core(ctx, grid, P->io_rho, P->io_eps, el, kind, P->io_phi, opts, rep, st, t0, P);
-  ck(cudaMemcpyAsync(phi_h, P->io_phi, b, cudaMemcpyDeviceToHost, st));
+  ck(cudaMemcpyAsync(P->own_rho, rho_h, b, cudaMemcpyHostToDevice, st));
+  ck(cudaMemcpyAsync(P->own_eps, eps_h, b, cudaMemcpyHostToDevice, st));
+  int s = solve_direct(*P, P->own_rho, P->own_eps, P->own_phi, kind, el, o, rep, st, t0);
+  ck(cudaMemcpyAsync(phi_h, P->own_phi, b, cudaMemcpyDeviceToHost, st));
   s = finish(s, st);
   if (rep) rep->time_ms = now_ms() - t0;
   return s;
@@ -896,22 +1351,29 @@ int gps_gpe_solve_host(gps_ctx* ctx, const gps_grid* grid, const double* rho_h, 
 int gps_setup_fields(gps_ctx* ctx, const gps_grid* grid, const double* eps, double* s_out,
                      double* q_out, void* stream) {
   if (!ctx || !eps || !s_out || !q_out) return GPS_ERR_INVALID;
+  int v = validate_grid(grid);
+  if (v != GPS_OK) return v;
   cudaStream_t st = (cudaStream_t)stream;
   GPS_GUARD_BEGIN
-  ProfScope prof_scope(ctx);
   cudaSetDevice(ctx->device);
-  Plan* P = nullptr;
-  int e = get_plan(ctx, grid, st, &P);
-  if (e != GPS_OK) return e;
-  setup_fields(P, eps, st);
-  read_scalars(P, st);
-  if (P->sc_host->bad_eps) {
-    ck(cudaMemsetAsync(&P->sc->bad_eps, 0, sizeof(int), st));
-    return finish(GPS_ERR_INVALID, st);
-  }
-  const size_t b = P->n * sizeof(double);
-  ck(cudaMemcpyAsync(s_out, P->s, b, cudaMemcpyDeviceToDevice, st));
-  ck(cudaMemcpyAsync(q_out, P->q, b, cudaMemcpyDeviceToDevice, st));
+  ProfScope prof_scope(ctx);
+  Pool* P = direct_pool(ctx, grid, st);
+  gps_opts o;
+  gps_default_opts(&o);
+  P->f.eps = const_cast<double*>(eps);
+  P->slot_req[0] = reinterpret_cast<Request*>(P);
+  put_state(*P, 0, initial_state(GPS_GPE, nullptr, o), st);
+  put_active(*P, st);
+  ensure_tuned(*P->shape, false, false, st);
+  launch_setup_group(*P, st);
+  get_states(*P, st);
+  ck(cudaStreamSynchronize(st));
+  P->slot_req[0] = nullptr;
+  P->f.eps = P->own_eps;
+  if (P->st_host[0].bad_eps) return finish(GPS_ERR_INVALID, st);
+  const size_t nb = P->n * sizeof(double);
+  ck(cudaMemcpyAsync(s_out, P->f.s, nb, cudaMemcpyDeviceToDevice, st));
+  ck(cudaMemcpyAsync(q_out, P->f.q, nb, cudaMemcpyDeviceToDevice, st));
   return finish(GPS_OK, st);
   GPS_GUARD_END
 }
@@ -919,14 +1381,20 @@ int gps_setup_fields(gps_ctx* ctx, const gps_grid* grid, const double* eps, doub
 int gps_vacuum_solve(gps_ctx* ctx, const gps_grid* grid, const double* sigma, double* w,
                      void* stream) {
   if (!ctx || !sigma || !w) return GPS_ERR_INVALID;
+  int v = validate_grid(grid);
+  if (v != GPS_OK) return v;
   cudaStream_t st = (cudaStream_t)stream;
   GPS_GUARD_BEGIN
-  ProfScope prof_scope(ctx);
   cudaSetDevice(ctx->device);
-  Plan* P = nullptr;
-  int e = get_plan(ctx, grid, st, &P);
-  if (e != GPS_OK) return e;
-  vacuum_pipeline<double2>(P, sigma, nullptr, P->table, 0.0, 0, w, nullptr, nullptr, false, st);
+  ProfScope prof_scope(ctx);
+  Pool* P = direct_pool(ctx, grid, st);
+  ensure_tuned(*P->shape, false, false, st);
+  Batch b{};
+  PipeArgs a{};
+  a.in = sigma;
+  a.out = w;
+  a.table = P->shape->table;
+  pipeline<double2>(*P, b, a, st);
   return finish(GPS_OK, st);
   GPS_GUARD_END
 }
@@ -934,20 +1402,25 @@ int gps_vacuum_solve(gps_ctx* ctx, const gps_grid* grid, const double* sigma, do
 int gps_precondition(gps_ctx* ctx, const gps_grid* grid, const double* s, const double* r, double* v,
                      int precision, void* stream) {
   if (!ctx || !s || !r || !v) return GPS_ERR_INVALID;
-  if (precision != GPS_FP64 && precision != GPS_MIXED) return GPS_ERR_INVALID;
+  if (precision < GPS_FP64 || precision > GPS_DF64) return GPS_ERR_INVALID;
+  int e = validate_grid(grid);
+  if (e != GPS_OK) return e;
   cudaStream_t st = (cudaStream_t)stream;
   GPS_GUARD_BEGIN
-  ProfScope prof_scope(ctx);
   cudaSetDevice(ctx->device);
-  Plan* P = nullptr;
-  int e = get_plan(ctx, grid, st, &P);
-  if (e != GPS_OK) return e;
-  if (precision == GPS_MIXED) {
-    ensure_w32(P);
-    vacuum_pipeline<float2>(P, r, s, P->table, 0.0, 0, v, s, nullptr, false, st);
-  } else {
-    vacuum_pipeline<double2>(P, r, s, P->table, 0.0, 0, v, s, nullptr, false, st);
-  }
+  ProfScope prof_scope(ctx);
+  Pool* P = direct_pool(ctx, grid, st);
+  ensure_tuned(*P->shape, precision == GPS_MIXED, precision == GPS_DF64, st);
+  Batch b{};
+  PipeArgs a{};
+  a.in = r;
+  a.in_scale = s;
+  a.out = v;
+  a.out_scale = s;
+  a.table = P->shape->table;
+  if (precision == GPS_MIXED) pipeline<float2>(*P, b, a, st);
+  else if (precision == GPS_DF64) pipeline<dfc>(*P, b, a, st);
+  else pipeline<double2>(*P, b, a, st);
   return finish(GPS_OK, st);
   GPS_GUARD_END
 }
@@ -965,6 +1438,109 @@ int gps_ionic_charge(gps_ctx* ctx, const gps_grid* grid, const double* phi, cons
   launch_ionic_charge(phi, eps, out, n, ion_params(el), st);
   return finish(GPS_OK, st);
   GPS_GUARD_END
+}
+
+int gps_batch_solve(gps_ctx* ctx, int count, const gps_request* reqs, gps_report* reps) {
+  if (!ctx || count < 0 || (count > 0 && !reqs)) return GPS_ERR_INVALID;
+  GPS_GUARD_BEGIN
+  cudaSetDevice(ctx->device);
+  const double t0 = now_ms();
+  Engine eng;
+  eng.device = ctx->device;
+  eng.budget = ctx->budget;
+  std::vector<std::unique_ptr<Request>> rs;
+  for (int i = 0; i < count; ++i) {
+    rs.emplace_back(new Request);
+    rs.back()->req = reqs[i];
+    rs.back()->t0 = t0;
+    eng.queue.push_back(rs.back().get());
+  }
+  while (eng.step() > 0) {
+  }
+  int status = GPS_OK;
+  for (int i = 0; i < count; ++i) {
+    if (reps) reps[i] = rs[i]->rep;
+    if (status == GPS_OK && rs[i]->status != GPS_OK) status = rs[i]->status;
+  }
+  return status;
+  GPS_GUARD_END
+}
+
+int gps_server_create(gps_server** out, int device, size_t budget, int max_slots) {
+  if (!out) return GPS_ERR_INVALID;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess) return GPS_ERR_CUDA;
+  if (device < 0 || device >= count || max_slots < 0) return GPS_ERR_INVALID;
+  gps_server* s = new (std::nothrow) gps_server;
+  if (!s) return GPS_ERR_NOMEM;
+  s->eng.device = device;
+  s->eng.budget = budget;
+  s->eng.max_slots = max_slots;
+  s->worker = std::thread([s] { s->loop(); });
+  *out = s;
+  return GPS_OK;
+}
+
+int gps_server_submit(gps_server* s, const gps_request* req, unsigned long long* ticket) {
+  if (!s || !req || !ticket) return GPS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->fatal != GPS_OK) return s->fatal;
+  auto r = std::make_unique<Request>();
+  r->req = *req;
+  r->t0 = now_ms();
+  r->ticket = s->next_ticket++;
+  *ticket = r->ticket;
+  s->incoming.push_back(r.get());
+  s->reqs.emplace(r->ticket, std::move(r));
+  s->cv.notify_all();
+  return GPS_OK;
+}
+
+int gps_server_poll(gps_server* s, unsigned long long ticket, gps_report* rep) {
+  if (!s) return GPS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return GPS_ERR_INVALID;
+  if (!it->second->done) return GPS_PENDING;
+  if (rep) *rep = it->second->rep;
+  const int st = it->second->status;
+  s->reqs.erase(it);
+  return st;
+}
+
+int gps_server_wait(gps_server* s, unsigned long long ticket, gps_report* rep) {
+  if (!s) return GPS_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return GPS_ERR_INVALID;
+  Request* r = it->second.get();
+  s->done_cv.wait(lk, [&] { return r->done; });
+  if (rep) *rep = r->rep;
+  const int st = r->status;
+  s->reqs.erase(ticket);
+  return st;
+}
+
+int gps_server_stats(gps_server* s, size_t* bytes, int* max_concurrent) {
+  if (!s) return GPS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (bytes) *bytes = s->eng.bytes();
+  if (max_concurrent) *max_concurrent = s->eng.max_concurrent;
+  return GPS_OK;
+}
+
+void gps_server_destroy(gps_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv.notify_all();
+  }
+  if (s->worker.joinable()) s->worker.join();
+  cudaSetDevice(s->eng.device);
+  cudaDeviceSynchronize();
+  delete s;
 }
 
 int gps_set_profiling(gps_ctx* ctx, int mask) {

@@ -8,13 +8,63 @@
 
 namespace gps {
 
+// Double-float number: the unevaluated sum hi + lo of two floats, |lo| <=
+// ulp(hi)/2, about 48 significant bits.  Arithmetic by error-free
+// transformations (Knuth's TwoSum, FMA-based TwoProd, Dekker's renormalizing
+// Fast2Sum) runs on the FP32 pipe, which on this GPU issues 64x the FP64
+// rate.  Addition uses the "sloppy" two-sum form: its error is bounded by
+// u^2 (|a| + |b|) (u = 2^-24), the norm-wise bound an FFT's error analysis
+// needs.
+using ::fma;
+
+struct df {
+  float hi, lo;
+  df() = default;
+  __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ explicit constexpr df(double d)
+      : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ explicit constexpr df(int i) : df((double)i) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return df(s, b - (s - a));
+}
+__device__ __forceinline__ df operator+(df a, df b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);   // TwoSum error of hi parts
+  return fast_two_sum(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);                     // TwoProd error
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df fma(df a, df b, df c) { return a * b + c; }
+
+// Complex double-float (16 bytes, the size of a double2).
+struct __align__(16) dfc {
+  df x, y;
+};
+
 template <typename V> struct Real;
 template <> struct Real<double2> { using T = double; };
 template <> struct Real<float2> { using T = float; };
+template <> struct Real<dfc> { using T = df; };
 
 template <typename V>
 __device__ __forceinline__ V mk(typename Real<V>::T x, typename Real<V>::T y) {
   V v; v.x = x; v.y = y; return v;
+}
+template <typename V> __device__ __forceinline__ V czero() {
+  using T = typename Real<V>::T;
+  return mk<V>(T(0), T(0));
 }
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
@@ -48,14 +98,13 @@ __device__ __forceinline__ double block_sum(double v) {
   return total;
 }
 
-__device__ __forceinline__ unsigned int linear_block() {
-  return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-}
-__device__ __forceinline__ unsigned int num_blocks() { return gridDim.x * gridDim.y * gridDim.z; }
+// Blocks of one slot: the x-y plane of the grid (blockIdx.z is the slot).
+__device__ __forceinline__ unsigned int linear_block() { return blockIdx.x + gridDim.x * blockIdx.y; }
+__device__ __forceinline__ unsigned int num_blocks() { return gridDim.x * gridDim.y; }
 
-// Deterministic grid reduction: every block stores its partial; the last block
-// to arrive (atomic ticket) sums all partials in a fixed order and returns
-// true in all of its threads with *result set.  The sum order does not depend
+// Deterministic grid reduction over the blocks of one slot: every block stores
+// its partial; the last block to arrive (atomic ticket) sums all partials in
+// a fixed order and returns true in all of its threads with *result set.  The sum order does not depend
 // on which block arrives last, so results are bitwise reproducible.
 __device__ __forceinline__ bool grid_reduce(double v, double* partials, unsigned int* counter,
                                             double* result) {
@@ -76,6 +125,89 @@ __device__ __forceinline__ bool grid_reduce(double v, double* partials, unsigned
   s = block_sum(s);
   if (threadIdx.x == 0) {
     *result = s;
+    *counter = 0u;
+  }
+  __syncthreads();
+  return true;
+}
+
+// Three sums over the blocks of one slot in one pass (one block reduction,
+// one atomic ticket, one last-block tail); same fixed-order determinism as
+// grid_reduce.
+__device__ __forceinline__ bool grid_reduce3(double a, double b, double c, double* pa, double* pb,
+                                             double* pc, unsigned int* counter, double* ra,
+                                             double* rb, double* rc) {
+  __shared__ double part[3][32];
+  __shared__ double tot[3];
+  __shared__ bool am_last;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    part[0][wid] = a;
+    part[1][wid] = b;
+    part[2][wid] = c;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    double x = lane < nw ? part[0][lane] : 0.0;
+    double y = lane < nw ? part[1][lane] : 0.0;
+    double z = lane < nw ? part[2][lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      y += __shfl_down_sync(0xffffffffu, y, o);
+      z += __shfl_down_sync(0xffffffffu, z, o);
+    }
+    if (lane == 0) {
+      const unsigned int lb = linear_block();
+      pa[lb] = x;
+      pb[lb] = y;
+      pc[lb] = z;
+      __threadfence();
+      const unsigned int t = atomicAdd(counter, 1u);
+      am_last = (t == num_blocks() - 1);
+    }
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  const unsigned int nb = num_blocks();
+  double x = 0.0, y = 0.0, z = 0.0;
+  for (unsigned int i = threadIdx.x; i < nb; i += blockDim.x) {
+    x += __ldcg(pa + i);
+    y += __ldcg(pb + i);
+    z += __ldcg(pc + i);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+    z += __shfl_down_sync(0xffffffffu, z, o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    part[0][wid] = x;
+    part[1][wid] = y;
+    part[2][wid] = z;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      sx += part[0][w];
+      sy += part[1][w];
+      sz += part[2][w];
+    }
+    tot[0] = sx;
+    tot[1] = sy;
+    tot[2] = sz;
+    *ra = sx;
+    *rb = sy;
+    *rc = sz;
     *counter = 0u;
   }
   __syncthreads();

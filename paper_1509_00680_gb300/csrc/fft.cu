@@ -109,6 +109,25 @@ template <typename V, int DIR> struct Dft<V, DIR, 5> {
   }
 };
 
+// Shared-memory layout of a line: one pad element after every 128 bytes
+// (8 complex doubles, 16 complex floats), so that the stride-R scatters of
+// the early Stockham stages spread over all banks.
+template <typename V> struct PadShift;
+template <> struct PadShift<double2> { static constexpr int v = 3; };
+template <> struct PadShift<float2> { static constexpr int v = 4; };
+template <> struct PadShift<dfc> { static constexpr int v = 3; };
+
+template <typename V> struct SpecOf;
+template <> struct SpecOf<double2> { static constexpr int v = SPEC_FP64; };
+template <> struct SpecOf<float2> { static constexpr int v = SPEC_FP32; };
+template <> struct SpecOf<dfc> { static constexpr int v = SPEC_DF64; };
+
+template <typename V>
+__device__ __forceinline__ int pidx(int i) { return i + (i >> PadShift<V>::v); }
+
+template <typename V>
+__host__ __device__ __forceinline__ int line_stride(int L) { return L + (L >> PadShift<V>::v) + 1; }
+
 // One Stockham stage over `nlines` lines of length L (line stride ls):
 // butterfly j gathers in[j + r L/R], twiddles by W_(Ns R)^(r k), k = j mod Ns,
 // and scatters to out[(j - k) R + k + r Ns].
@@ -125,7 +144,7 @@ __device__ __forceinline__ void stage(const V* __restrict__ in, V* __restrict__ 
     V* dst = out + line * ls;
     V x[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = src[j + r * nb];
+    for (int r = 0; r < R; ++r) x[r] = src[pidx<V>(j + r * nb)];
     const int k = j % Ns;
     if (k != 0) {
       const int step = tstep * k;
@@ -138,7 +157,7 @@ __device__ __forceinline__ void stage(const V* __restrict__ in, V* __restrict__ 
     Dft<V, DIR, R>::run(x);
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[base + r * Ns] = x[r];
+    for (int r = 0; r < R; ++r) dst[pidx<V>(base + r * Ns)] = x[r];
   }
 }
 
@@ -172,18 +191,27 @@ __device__ __forceinline__ size_t row_offset(const PassGeom& g, int row) {
 
 constexpr int kThreads = 256;
 
+// Slot served by this block for a spectrum pass of precision V, or -1.
+template <typename V>
+__device__ __forceinline__ int pass_slot(const Batch& b) {
+  int s = batch_slot(b);
+  if (s >= 0 && b.st && b.prec >= 0 && b.st[s].spec != SpecOf<V>::v) s = -1;
+  if (s >= 0) mark_acted(b);
+  return s;
+}
+
 template <typename V>
 __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, const V* __restrict__ twg,
-                                                   const double* __restrict__ in,
-                                                   const double* __restrict__ scale,
-                                                   V* __restrict__ W, const int* __restrict__ done,
-                                                   double* __restrict__ partials, PcgScalars* sc,
-                                                   double* sum_out) {
+                                                   Batch b, PipeArgs a) {
   using T = typename Real<V>::T;
-  if (done && *done) return;
+  const int slot = pass_slot<V>(b);
+  if (slot < 0) return;
+  const double* __restrict__ in = a.in + slot * b.vstride;
+  const double* __restrict__ scale = a.in_scale ? a.in_scale + slot * b.vstride : nullptr;
+  V* __restrict__ W = reinterpret_cast<V*>(a.W) + slot * a.wstride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
-  const int L = s.L, ls = L + 1;
+  const int L = s.L, ls = line_stride<V>(L);
   V* b0 = tw + L;
   V* b1 = b0 + g.lines_x * ls;
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
@@ -194,127 +222,127 @@ __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, cons
   for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
     const int l = idx / L, j = idx - l * L;
     const int ra = 2 * (p0 + l);
-    double a = 0.0, b = 0.0;
+    double va = 0.0, vb = 0.0;
     if (j < g.nx) {
       const size_t oa = (size_t)ra * g.nx + j;
-      a = in[oa];
-      if (scale) a *= scale[oa];
+      va = in[oa];
+      if (scale) va *= scale[oa];
       if (ra + 1 < g.nrows) {
-        b = in[oa + g.nx];
-        if (scale) b *= scale[oa + g.nx];
+        vb = in[oa + g.nx];
+        if (scale) vb *= scale[oa + g.nx];
       }
     }
-    sum += a + b;
-    b0[l * ls + j] = mk<V>((T)a, (T)b);
+    sum += va + vb;
+    b0[l * ls + pidx<V>(j)] = mk<V>((T)va, (T)vb);
   }
   __syncthreads();
   const V* res = fft_lines<V, -1>(b0, b1, s, ls, nl, tw);
   for (int idx = threadIdx.x; idx < nl * g.Hx; idx += blockDim.x) {
     const int l = idx / g.Hx, k = idx - l * g.Hx;
-    const V zk = res[l * ls + k];
-    const V zm = res[l * ls + (k == 0 ? 0 : L - k)];
+    const V zk = res[l * ls + pidx<V>(k)];
+    const V zm = res[l * ls + pidx<V>(k == 0 ? 0 : L - k)];
     const int ra = 2 * (p0 + l);
     // A_k = (Z_k + conj Z_(L-k))/2 ; B_k = -i (Z_k - conj Z_(L-k))/2
     W[row_offset(g, ra) + k] = mk<V>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
     if (ra + 1 < g.nrows) W[row_offset(g, ra + 1) + k] = mk<V>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
   }
-  if (sum_out) grid_reduce(sum, partials, &sc->counter[CNT_MU], sum_out);
+  if (a.red_mu && b.st)
+    grid_reduce(sum, b.partials + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_MU], &b.st[slot].mu_sum);
 }
 
 template <typename V, int DIR>
 __global__ void __launch_bounds__(kThreads) k_y(PassGeom g, FftSched s, const V* __restrict__ twg,
-                                               V* __restrict__ W, const int* __restrict__ done) {
-  if (done && *done) return;
+                                               Batch b, PipeArgs a) {
+  const int slot = pass_slot<V>(b);
+  if (slot < 0) return;
+  V* __restrict__ W = reinterpret_cast<V*>(a.W) + slot * a.wstride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
-  const int L = s.L, ls = L + 1, tile = g.tile_y;
+  const int L = s.L, ls = line_stride<V>(L), tile = g.tile_y;
   V* b0 = tw + L;
   V* b1 = b0 + tile * ls;
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
   const int kx0 = blockIdx.x * tile;
+  const int nl = min(tile, g.Hx - kx0);   // valid columns of this tile
   const int z = blockIdx.y;
   const size_t plane = (size_t)z * g.Py * g.Hx;
   const int nload = DIR < 0 ? g.ny : L;   // forward: rows y >= ny are the zero padding
-  for (int idx = threadIdx.x; idx < tile * L; idx += blockDim.x) {
-    const int y = idx / tile, c = idx - y * tile;
-    const int kx = kx0 + c;
-    V v = mk<V>(0, 0);
-    if (kx < g.Hx && y < nload) v = W[plane + (size_t)y * g.Hx + kx];
-    b0[c * ls + y] = v;
+  for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+    const int y = idx / nl, c = idx - y * nl;
+    V v = czero<V>();
+    if (y < nload) v = W[plane + (size_t)y * g.Hx + kx0 + c];
+    b0[c * ls + pidx<V>(y)] = v;
   }
   __syncthreads();
-  const V* res = fft_lines<V, DIR>(b0, b1, s, ls, tile, tw);
+  const V* res = fft_lines<V, DIR>(b0, b1, s, ls, nl, tw);
   const int nstore = DIR < 0 ? L : g.ny;  // inverse: crop to y < ny
-  for (int idx = threadIdx.x; idx < tile * nstore; idx += blockDim.x) {
-    const int y = idx / tile, c = idx - y * tile;
-    const int kx = kx0 + c;
-    if (kx < g.Hx) W[plane + (size_t)y * g.Hx + kx] = res[c * ls + y];
+  for (int idx = threadIdx.x; idx < nl * nstore; idx += blockDim.x) {
+    const int y = idx / nl, c = idx - y * nl;
+    W[plane + (size_t)y * g.Hx + kx0 + c] = res[c * ls + pidx<V>(y)];
   }
 }
 
 template <typename V>
 __global__ void __launch_bounds__(kThreads) k_z(PassGeom g, FftSched s, const V* __restrict__ twg,
-                                               V* __restrict__ W, const double* __restrict__ table,
-                                               double k0, int use_k0, double* __restrict__ mu_sum,
-                                               const int* __restrict__ done) {
+                                               Batch b, PipeArgs a) {
   using T = typename Real<V>::T;
-  if (done && *done) return;
+  const int slot = pass_slot<V>(b);
+  if (slot < 0) return;
+  V* __restrict__ W = reinterpret_cast<V*>(a.W) + slot * a.wstride;
+  const bool use_k0 = a.slot_k0 && b.st && b.st[slot].use_k0;
+  const double k0 = use_k0 ? b.st[slot].k0 : 0.0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
-  const int L = s.L, ls = L + 1, tile = g.tile_z;
+  const int L = s.L, ls = line_stride<V>(L), tile = g.tile_z;
   V* b0 = tw + L;
   V* b1 = b0 + tile * ls;
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
   const int kx0 = blockIdx.x * tile;
+  const int nl = min(tile, g.Hx - kx0);
   const int ky = blockIdx.y;
-  const size_t colbase = (size_t)ky * g.Hx;
+  const size_t colbase = (size_t)ky * g.Hx + kx0;
   const size_t zstride = (size_t)g.Py * g.Hx;
-  for (int idx = threadIdx.x; idx < tile * L; idx += blockDim.x) {
-    const int z = idx / tile, c = idx - z * tile;
-    const int kx = kx0 + c;
-    V v = mk<V>(0, 0);
-    if (kx < g.Hx && z < g.nz) v = W[(size_t)z * zstride + colbase + kx];
-    b0[c * ls + z] = v;
+  for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+    const int z = idx / nl, c = idx - z * nl;
+    V v = czero<V>();
+    if (z < g.nz) v = W[(size_t)z * zstride + colbase + c];
+    b0[c * ls + pidx<V>(z)] = v;
   }
   __syncthreads();
-  V* res = fft_lines<V, -1>(b0, b1, s, ls, tile, tw);
+  V* res = fft_lines<V, -1>(b0, b1, s, ls, nl, tw);
   V* other = (res == b0) ? b1 : b0;
-  if (mu_sum && ky == 0 && blockIdx.x == 0 && threadIdx.x == 0) *mu_sum = (double)res[0].x;
   const int kyp = min(ky, g.Py - ky);
   const int hy = g.Py / 2 + 1;
-  for (int idx = threadIdx.x; idx < tile * L; idx += blockDim.x) {
-    const int kz = idx / tile, c = idx - kz * tile;
+  for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+    const int kz = idx / nl, c = idx - kz * nl;
     const int kx = kx0 + c;
-    if (kx < g.Hx) {
-      const int kzp = min(kz, L - kz);
-      double t = table[((size_t)kzp * hy + kyp) * g.Hx + kx];
-      if (use_k0 && kx == 0 && ky == 0 && kz == 0) t = k0;
-      res[c * ls + kz] = cscale(res[c * ls + kz], (T)t);
-    }
+    const int kzp = min(kz, L - kz);
+    double t = a.table[((size_t)kzp * hy + kyp) * g.Hx + kx];
+    if (use_k0 && kx == 0 && ky == 0 && kz == 0) t = k0;
+    const int pk = c * ls + pidx<V>(kz);
+    res[pk] = cscale(res[pk], (T)t);
   }
   __syncthreads();
-  const V* fin = fft_lines<V, +1>(res, other, s, ls, tile, tw);
-  for (int idx = threadIdx.x; idx < tile * g.nz; idx += blockDim.x) {
-    const int z = idx / tile, c = idx - z * tile;
-    const int kx = kx0 + c;
-    if (kx < g.Hx) W[(size_t)z * zstride + colbase + kx] = fin[c * ls + z];
+  const V* fin = fft_lines<V, +1>(res, other, s, ls, nl, tw);
+  for (int idx = threadIdx.x; idx < nl * g.nz; idx += blockDim.x) {
+    const int z = idx / nl, c = idx - z * nl;
+    W[(size_t)z * zstride + colbase + c] = fin[c * ls + pidx<V>(z)];
   }
 }
 
 template <typename V>
 __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, const V* __restrict__ twg,
-                                                   const V* __restrict__ W, double* __restrict__ out,
-                                                   const double* __restrict__ out_scale,
-                                                   const double* __restrict__ dot_with,
-                                                   double* __restrict__ partials, PcgScalars* sc,
-                                                   int slot, double* dot_out,
-                                                   const int* __restrict__ done,
-                                                   double* __restrict__ partials2, double* wsum_out) {
+                                                   Batch b, PipeArgs a) {
   using T = typename Real<V>::T;
-  if (done && *done) return;
+  const int slot = pass_slot<V>(b);
+  if (slot < 0) return;
+  const V* __restrict__ W = reinterpret_cast<const V*>(a.W) + slot * a.wstride;
+  double* __restrict__ out = a.out + slot * b.vstride;
+  const double* __restrict__ out_scale = a.out_scale ? a.out_scale + slot * b.vstride : nullptr;
+  const double* __restrict__ dot_with = a.dot_with ? a.dot_with + slot * b.vstride : nullptr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
-  const int L = s.L, ls = L + 1;
+  const int L = s.L, ls = line_stride<V>(L);
   V* b0 = tw + L;
   V* b1 = b0 + g.lines_x * ls;
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
@@ -328,14 +356,14 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
     V A, B;
     if (k < g.Hx) {
       A = W[row_offset(g, ra) + k];
-      B = hasb ? W[row_offset(g, ra + 1) + k] : mk<V>(0, 0);
-      if (k == 0 || 2 * k == L) { A.y = 0; B.y = 0; }   // DC and Nyquist are real
+      B = hasb ? W[row_offset(g, ra + 1) + k] : czero<V>();
+      if (k == 0 || 2 * k == L) { A.y = T(0); B.y = T(0); }   // DC and Nyquist are real
     } else {
       const int m = L - k;
       A = cconj(W[row_offset(g, ra) + m]);
-      B = hasb ? cconj(W[row_offset(g, ra + 1) + m]) : mk<V>(0, 0);
+      B = hasb ? cconj(W[row_offset(g, ra + 1) + m]) : czero<V>();
     }
-    b0[l * ls + k] = mk<V>(A.x - B.y, A.y + B.x);   // Z = A + i B
+    b0[l * ls + pidx<V>(k)] = mk<V>(A.x - B.y, A.y + B.x);   // Z = A + i B
   }
   __syncthreads();
   const V* res = fft_lines<V, +1>(b0, b1, s, ls, nl, tw);
@@ -343,30 +371,40 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
   for (int idx = threadIdx.x; idx < nl * g.nx; idx += blockDim.x) {
     const int l = idx / g.nx, j = idx - l * g.nx;
     const int ra = 2 * (p0 + l);
-    const V zz = res[l * ls + j];
+    const V zz = res[l * ls + pidx<V>(j)];
     const size_t oa = (size_t)ra * g.nx + j;
-    wsum += (double)zz.x + ((ra + 1 < g.nrows) ? (double)zz.y : 0.0);
+    wsum += (double)zz.x;
     double va = (double)zz.x;
     if (out_scale) va *= out_scale[oa];
     out[oa] = va;
     if (dot_with) dot += va * dot_with[oa];
     if (ra + 1 < g.nrows) {
       const size_t ob = oa + g.nx;
+      wsum += (double)zz.y;
       double vb = (double)zz.y;
       if (out_scale) vb *= out_scale[ob];
       out[ob] = vb;
       if (dot_with) dot += vb * dot_with[ob];
     }
   }
-  if (partials) grid_reduce(dot, partials, &sc->counter[slot], dot_out);
-  if (wsum_out) grid_reduce(wsum, partials2, &sc->counter[CNT_WSUM], wsum_out);
+  if (dot_with && b.st)
+    grid_reduce(dot, b.partials + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_VR], &b.st[slot].vr);
+  if (a.red_wsum && b.st && b.st[slot].gauge)
+    grid_reduce(wsum, b.partials2 + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_WSUM],
+                &b.st[slot].wsum);
 }
 
 // ---------------------------------------------------------------------------
 // Launchers.
 
 size_t x_lines_smem_bytes(int L, int lines, size_t vbytes) {
-  return (size_t)(L + 2 * lines * (L + 1)) * vbytes;
+  const int ls = vbytes == sizeof(double2) ? line_stride<double2>(L) : line_stride<float2>(L);
+  return (size_t)(L + 2 * lines * ls) * vbytes;
+}
+
+int x_pass_blocks(const PassGeom& g) {
+  const int npairs = (g.nrows + 1) / 2;
+  return (npairs + g.lines_x - 1) / g.lines_x;
 }
 
 template <typename K>
@@ -375,70 +413,60 @@ static void set_smem(K kernel, size_t bytes) {
 }
 
 template <typename V>
-void launch_x_fwd(const PassGeom& g, const FftSched& s, const V* tw, const double* in,
-                  const double* scale, V* W, const int* done, cudaStream_t st, double* partials,
-                  PcgScalars* sc, double* sum_out) {
-  const int npairs = (g.nrows + 1) / 2;
-  const int blocks = (npairs + g.lines_x - 1) / g.lines_x;
+void launch_x_fwd(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
+                  const PipeArgs& a, int nslots, cudaStream_t st) {
   const size_t sm = x_lines_smem_bytes(s.L, g.lines_x, sizeof(V));
   set_smem(k_x_fwd<V>, sm);
   count_launch();
-  k_x_fwd<V><<<blocks, kThreads, sm, st>>>(g, s, tw, in, scale, W, done, partials, sc, sum_out);
+  k_x_fwd<V><<<dim3(x_pass_blocks(g), 1, nslots), kThreads, sm, st>>>(g, s, tw, b, a);
 }
 
 template <typename V>
-void launch_y(const PassGeom& g, const FftSched& s, const V* tw, V* W, bool inverse,
-              const int* done, cudaStream_t st) {
-  dim3 grid((g.Hx + g.tile_y - 1) / g.tile_y, g.nz);
+void launch_y(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
+              const PipeArgs& a, bool inverse, int nslots, cudaStream_t st) {
+  dim3 grid((g.Hx + g.tile_y - 1) / g.tile_y, g.nz, nslots);
   const size_t sm = x_lines_smem_bytes(s.L, g.tile_y, sizeof(V));
+  count_launch();
   if (inverse) {
     set_smem(k_y<V, +1>, sm);
-    count_launch();
-    k_y<V, +1><<<grid, kThreads, sm, st>>>(g, s, tw, W, done);
+    k_y<V, +1><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
   } else {
     set_smem(k_y<V, -1>, sm);
-    count_launch();
-    k_y<V, -1><<<grid, kThreads, sm, st>>>(g, s, tw, W, done);
+    k_y<V, -1><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
   }
 }
 
 template <typename V>
-void launch_z(const PassGeom& g, const FftSched& s, const V* tw, V* W, const double* table,
-              double k0_override, int use_k0, double* mu_sum, const int* done, cudaStream_t st) {
-  dim3 grid((g.Hx + g.tile_z - 1) / g.tile_z, g.Py);
+void launch_z(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
+              const PipeArgs& a, int nslots, cudaStream_t st) {
+  dim3 grid((g.Hx + g.tile_z - 1) / g.tile_z, g.Py, nslots);
   const size_t sm = x_lines_smem_bytes(s.L, g.tile_z, sizeof(V));
   set_smem(k_z<V>, sm);
   count_launch();
-  k_z<V><<<grid, kThreads, sm, st>>>(g, s, tw, W, table, k0_override, use_k0, mu_sum, done);
+  k_z<V><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
 }
 
 template <typename V>
-void launch_x_inv(const PassGeom& g, const FftSched& s, const V* tw, const V* W, double* out,
-                  const double* out_scale, const double* dot_with, double* partials,
-                  PcgScalars* sc, int counter_slot, double* dot_out, const int* done,
-                  cudaStream_t st, double* partials2, double* wsum_out) {
-  const int npairs = (g.nrows + 1) / 2;
-  const int blocks = (npairs + g.lines_x - 1) / g.lines_x;
+void launch_x_inv(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
+                  const PipeArgs& a, int nslots, cudaStream_t st) {
   const size_t sm = x_lines_smem_bytes(s.L, g.lines_x, sizeof(V));
   set_smem(k_x_inv<V>, sm);
   count_launch();
-  k_x_inv<V><<<blocks, kThreads, sm, st>>>(g, s, tw, W, out, out_scale, dot_with, partials, sc,
-                                           counter_slot, dot_out, done, partials2, wsum_out);
+  k_x_inv<V><<<dim3(x_pass_blocks(g), 1, nslots), kThreads, sm, st>>>(g, s, tw, b, a);
 }
 
-#define GPS_INSTANTIATE(V)                                                                        \
-  template void launch_x_fwd<V>(const PassGeom&, const FftSched&, const V*, const double*,        \
-                                const double*, V*, const int*, cudaStream_t, double*, PcgScalars*, \
-                                double*);                                                          \
-  template void launch_y<V>(const PassGeom&, const FftSched&, const V*, V*, bool, const int*,     \
-                            cudaStream_t);                                                        \
-  template void launch_z<V>(const PassGeom&, const FftSched&, const V*, V*, const double*, double, \
-                            int, double*, const int*, cudaStream_t);                              \
-  template void launch_x_inv<V>(const PassGeom&, const FftSched&, const V*, const V*, double*,    \
-                                const double*, const double*, double*, PcgScalars*, int, double*, \
-                                const int*, cudaStream_t, double*, double*);
+#define GPS_INSTANTIATE(V)                                                                       \
+  template void launch_x_fwd<V>(const PassGeom&, const FftSched&, const V*, const Batch&,       \
+                                const PipeArgs&, int, cudaStream_t);                             \
+  template void launch_y<V>(const PassGeom&, const FftSched&, const V*, const Batch&,           \
+                            const PipeArgs&, bool, int, cudaStream_t);                           \
+  template void launch_z<V>(const PassGeom&, const FftSched&, const V*, const Batch&,           \
+                            const PipeArgs&, int, cudaStream_t);                                 \
+  template void launch_x_inv<V>(const PassGeom&, const FftSched&, const V*, const Batch&,       \
+                                const PipeArgs&, int, cudaStream_t);
 
 GPS_INSTANTIATE(double2)
 GPS_INSTANTIATE(float2)
+GPS_INSTANTIATE(dfc)
 
 }  // namespace gps

@@ -1,4 +1,11 @@
 // Internal declarations of the GB300 solver library (not part of the ABI).
+//
+// Every solve runs in a slot of a pool.  A pool holds the per-shape data
+// (FFT schedules, twiddles, Green's table) and `capacity` slots; each slot
+// owns strided vectors, a spectrum workspace, reduction partials and a
+// SlotState.  Kernels carry a batch dimension: blockIdx.z indexes a
+// device-side active list of slots, and each kernel acts only on slots whose
+// phase matches the phase it serves.  A single solve is a pool of one slot.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,67 +28,134 @@ struct FftSched {
   int ns[kMaxStages];   // product of the radices of the previous stages
 };
 
-// Device scalars of one PCG run (Algorithm 2).  Written by the last block of
-// the reducing kernels, read by every block of the following kernels.
-struct PcgScalars {
-  double vr, vr_prev, pAp, alpha, beta, rr, rr0, tol2;
-  double mu_sum;        // periodic: sum of s*r over the grid (FP64, x pass)
-  double wsum;          // periodic: sum of w = sqrt(eps) v over the grid (x inverse pass)
-  double background;    // periodic GPe: mean of rho removed
-  double aux[8];        // scratch results of one-off reductions
-  int iter, done, status, max_iter;
-  int bad_eps;          // set if an eps value is not positive
-  int pad_;
-  unsigned int counter[8];
+// Spectrum precision of a slot: FP64, FP32, or double-float on the FP32 pipe.
+enum Spec { SPEC_FP64 = 0, SPEC_FP32 = 1, SPEC_DF64 = 2 };
+
+// Per-slot phases of the device state machine.
+enum Phase {
+  PH_IDLE = 0,     // free or finished and collected
+  PH_SETUP = 1,    // s, sqrt(eps), q, q + lambda
+  PH_INIT = 2,     // r_0 of the next PCG
+  PH_ITER = 3,     // Algorithm 2 iterations
+  PH_NLEVAL = 4,   // nonlinear PB: fresh ionic charge, outer residual, next source
+  PH_TRIAL = 5,    // nonlinear PB: residual at a trial step t
+  PH_COMMIT = 6,   // nonlinear PB: apply the accepted step
+  PH_CERT = 7,     // FP64 certificate of the result
+  PH_DONE = 8      // result ready for the host
 };
 
-enum Counter { CNT_VR = 0, CNT_PAP = 1, CNT_RR = 2, CNT_AUX = 3, CNT_AUX2 = 4, CNT_MU = 5,
-               CNT_WSUM = 6 };
+enum Counter {
+  CNT_VR = 0, CNT_PAP, CNT_RR, CNT_AUX, CNT_AUX2, CNT_MU, CNT_WSUM, CNT_AUX3, CNT_APSUM, CNT_PSUM,
+  CNT_COUNT
+};
 
 // Precomputed factors of the ionic charge (Eqs. rhoions, ionsconcPB).
 struct IonParams {
   int nspecies;
-  double zq[GPS_MAX_SPECIES];    // valences
-  double zn[GPS_MAX_SPECIES];    // z_i * n_i  (bohr^-3)
+  double zq[GPS_MAX_SPECIES];      // valences
+  double zn[GPS_MAX_SPECIES];      // z_i * n_i  (bohr^-3)
   double z2n_kt[GPS_MAX_SPECIES];  // z_i^2 n_i / kT
   double inv_kt;
-  double inv_eps0m1;             // 1/(eps0 - 1)
+  double inv_eps0m1;               // 1/(eps0 - 1)
   double exp_cap;
+  double lambda0;                  // 4 pi sum z_i^2 n_i / kT
 };
 
-// One FFT pass configuration shared by the pass kernels.
+// Device state of one slot (one request).
+struct SlotState {
+  IonParams ion;
+  // PCG (Algorithm 2)
+  double vr, vr_prev, pAp, alpha, beta, rr, rr0, tol2;
+  double mu_sum;        // periodic: sum of s*r (FP64, x pass)
+  double wsum;          // periodic GPe: sum of w = sqrt(eps) v (x inverse pass)
+  double background;    // periodic GPe: mean of rho removed
+  double k0;            // periodic linear operator: k = 0 value of the normalized kernel
+  double tol_abs, tol_rel, mixed_switch;
+  double aux[8];        // results of one-off reductions
+  // nonlinear PB (Algorithm 4)
+  double F, F0, t, tol_outer, eta, forcing, lam_sum, eps_sum;
+  double cert;          // ||g|| / ||phi||, -1 if not computed
+  double rr_min;        // smallest ||r||^2 seen in the FP32 phase
+  double ap_mean;       // periodic GPe: grid mean of A p removed in the r update
+  double ap_sum, p_sum;
+  int stall;            // FP32 iterations since the last new minimum
+  int phase, kind, status;
+  int iter, max_iter, iters_total, fp64_iters;
+  int use_k0, neutralize, gauge;
+  int mixed, spec, spec_hi, restart, certify;   // spec: spectrum precision in use
+  int newton, outer, max_outer, bad_eps;
+  unsigned int counter[CNT_COUNT];
+};
+
+// Geometry of the FFT passes, shared by every slot of a pool.
 struct PassGeom {
   int nx, ny, nz;      // real grid
   int Px, Py, Pz;      // padded transform lengths
   int Hx;              // Px/2 + 1
   int nrows;           // ny*nz (rows of the x passes)
-  int lines_x;         // lines per CTA in x passes (row pairs)
+  int lines_x;         // row pairs per CTA in the x passes
   int tile_y, tile_z;  // columns per CTA in the y / z passes
 };
 
-template <typename V>
-struct SpecBuf {
-  V* W;                // [nz][Py][Hx] complex
+// Slot addressing of one launch.  active == nullptr: slot 0 only, no phase
+// test (st may then be nullptr too).
+struct Batch {
+  const int* active;   // active[0] = count, active[1 + i] = slot id
+  SlotState* st;       // per-slot states (array of capacity)
+  int phase;           // the phase this launch serves
+  int prec;            // FFT passes: serve slots whose spectrum precision is prec, -1 any
+  size_t vstride;      // elements between slots in every vector
+  double* partials;    // reduction partials, pstride per slot
+  double* partials2;
+  double* partials3;
+  int pstride;
+  int* acted;          // optional: set to 1 by a block that served a slot (profiling)
 };
 
+// Field roles of one spectrum-pipeline launch (base pointers of slot 0).
+struct PipeArgs {
+  const double* in;         // x_fwd input
+  const double* in_scale;   // optional factor (s)
+  double* out;              // x_inv output
+  const double* out_scale;  // optional factor (s or sqrt(eps))
+  const double* dot_with;   // optional: reduce (out, dot_with) into st.vr
+  const double* table;      // normalized octant Green's / Laplacian table
+  void* W;                  // spectrum base (slot 0)
+  size_t wstride;           // complex elements between slots
+  int slot_k0;              // use st[slot].k0 for k = 0 when st[slot].use_k0
+  int red_mu;               // reduce sum(in * in_scale) into st.mu_sum (x_fwd)
+  int red_wsum;             // reduce sum of unscaled output into st.wsum (x_inv)
+};
+
+// Block prologue: slot served by this block, or -1.
+__device__ __forceinline__ int batch_slot(const Batch& b) {
+  if (!b.active) return blockIdx.z == 0 ? 0 : -1;
+  if ((int)blockIdx.z >= b.active[0]) return -1;
+  const int s = b.active[1 + blockIdx.z];
+  if (b.st && b.st[s].phase != b.phase) return -1;
+  return s;
+}
+
+// Records that this launch did work for some slot (profiling only).
+__device__ __forceinline__ void mark_acted(const Batch& b) {
+  if (b.acted && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) *b.acted = 1;
+}
+
 // ---- FFT pass launchers (fft.cu) -----------------------------------------
-// Forward x pass: rows of in (optionally scaled by scale) -> half spectra.
 template <typename V>
-void launch_x_fwd(const PassGeom& g, const FftSched& s, const V* tw, const double* in,
-                  const double* scale, V* W, const int* done, cudaStream_t st,
-                  double* partials = nullptr, PcgScalars* sc = nullptr, double* sum_out = nullptr);
+void launch_x_fwd(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
+                  const PipeArgs& a, int nslots, cudaStream_t st);
 template <typename V>
-void launch_y(const PassGeom& g, const FftSched& s, const V* tw, V* W, bool inverse,
-              const int* done, cudaStream_t st);
+void launch_y(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
+              const PipeArgs& a, bool inverse, int nslots, cudaStream_t st);
 template <typename V>
-void launch_z(const PassGeom& g, const FftSched& s, const V* tw, V* W, const double* table,
-              double k0_override, int use_k0, double* mu_sum, const int* done, cudaStream_t st);
+void launch_z(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
+              const PipeArgs& a, int nslots, cudaStream_t st);
 template <typename V>
-void launch_x_inv(const PassGeom& g, const FftSched& s, const V* tw, const V* W, double* out,
-                  const double* out_scale, const double* dot_with, double* partials,
-                  PcgScalars* sc, int counter_slot, double* dot_out, const int* done,
-                  cudaStream_t st, double* partials2 = nullptr, double* wsum_out = nullptr);
+void launch_x_inv(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
+                  const PipeArgs& a, int nslots, cudaStream_t st);
 size_t x_lines_smem_bytes(int L, int lines, size_t vbytes);
+int x_pass_blocks(const PassGeom& g);
 
 // ---- kernels.cu ------------------------------------------------------------
 int grid_blocks(size_t n, int threads);

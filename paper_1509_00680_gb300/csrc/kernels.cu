@@ -1,13 +1,22 @@
-// Pointwise, stencil, reduction and table kernels of the PCG solver.
+// Pointwise, stencil, reduction and table kernels of the PCG solver, in
+// batched slot form (see gps_internal.h), and the device-side phase machine
+// of every slot:
 //
-//   setup        s = eps^-1/2, sqrt(eps); q = sqrt(eps) lap sqrt(eps) by the
-//                order-16 central stencil (Sec. "Numerical results")
-//   PCG updates  Algorithm 2 with the operator identity of Eq. (corr)/(corrPB)
-//   ions         Eqs. (rhoions, ionsconcPB) and the outer step of Algorithm 4
-//   tables       vacuum Green's-function tables for the three BCs
+//   SETUP   s = eps^-1/2, sqrt(eps); q = sqrt(eps) lap sqrt(eps) by the
+//           order-16 stencil (free/surface; periodic uses the spectrum
+//           pipeline); q + lambda (Eq. corrPB)            -> INIT | NLEVAL
+//   INIT    r_0 = -4 pi (source - background)                 -> ITER
+//   ITER    Algorithm 2 with the identity of Eq. corr / corrPB
+//                                   -> TRIAL | COMMIT (NLPB), CERT | DONE
+//   NLEVAL  fresh ionic charge (Eqs. rhoions, ionsconcPB), outer residual,
+//           next inner source (Algorithm 4)           -> INIT | CERT | DONE
+//   TRIAL   outer residual at the trial step t (Newton line search)
+//   COMMIT  apply the step                                   -> NLEVAL
+//   CERT    FP64 certificate g = M(src - qlam phi/4pi) [+ c s] - phi -> DONE
 //
-// Every reduction is deterministic (fixed-order per-block partials combined by
-// the last block), so repeated solves are bitwise identical.
+// Phase changes are made by the last block of a slot's reduction, after every
+// block of that slot has finished, so launches later in the same stream see
+// them.  Every reduction is deterministic (fixed-order partials).
 #include <atomic>
 #include <cmath>
 
@@ -31,27 +40,78 @@ int grid_blocks(size_t n, int threads) {
   return (int)b;
 }
 
+// Blocks per slot for the vector kernels.  It depends on the grid only, not
+// on how many slots share the launch, so every slot reduces in the same order
+// alone and in a batch (bitwise identical results).
+int vec_blocks(size_t n, int nslots) {
+  (void)nslots;
+  return grid_blocks(n, kT);
+}
+
 #define GRID_STRIDE(i, n) \
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
 
+#define SLOT_PROLOGUE(b)                  \
+  const int slot = batch_slot(b);         \
+  if (slot < 0) return;                   \
+  mark_acted(b);                          \
+  SlotState& S = b.st[slot];              \
+  const size_t off = (size_t)slot * b.vstride;
+
+__device__ __forceinline__ double* slot_partials(const Batch& b, int slot) {
+  return b.partials + (size_t)slot * b.pstride;
+}
+__device__ __forceinline__ double* slot_partials2(const Batch& b, int slot) {
+  return b.partials2 + (size_t)slot * b.pstride;
+}
+__device__ __forceinline__ double* slot_partials3(const Batch& b, int slot) {
+  return b.partials3 + (size_t)slot * b.pstride;
+}
+
+// State after a PCG has stopped (converged, failed or out of iterations).
+__device__ void after_pcg(SlotState& S) {
+  if (S.kind == GPS_NLPB) {
+    if (S.status == GPS_ERR_BREAKDOWN) {
+      S.phase = PH_DONE;
+      return;
+    }
+    S.status = GPS_OK;          // an inexact inner solve is a valid Newton / mixing step
+    S.t = 1.0;
+    S.phase = S.newton ? PH_TRIAL : PH_COMMIT;
+    return;
+  }
+  S.phase = (S.status == GPS_OK && S.certify) ? PH_CERT : PH_DONE;
+}
+
 // ------------------------------------------------------------------ setup --
 
-__global__ void k_setup_s(const double* __restrict__ eps, double* __restrict__ s,
-                          double* __restrict__ sq, size_t n, PcgScalars* sc) {
+__global__ void k_setup_s(Batch b, Fields f, size_t n) {
+  SLOT_PROLOGUE(b)
+  const double* eps = f.eps + off;
+  double* s = f.s + off;
+  double* sq = f.sq + off;
+  double acc = 0.0;
+  int bad = 0;
   GRID_STRIDE(i, n) {
     const double e = eps[i];
-    if (!(e > 0.0)) sc->bad_eps = 1;
+    if (!(e > 0.0)) bad = 1;
     const double r = sqrt(e);
     sq[i] = r;
     s[i] = 1.0 / r;
+    acc += e;
   }
+  if (bad) S.bad_eps = 1;
+  grid_reduce(acc, slot_partials(b, slot), &S.counter[CNT_AUX], &S.eps_sum);
 }
 
 // q = sqrt(eps) * sum_axes (1/h^2) sum_j c_|j| sqrt(eps)(i + j e_axis).
 // Free axes continue the field by its face value; periodic axes wrap.
-__global__ void k_fd16_q(const double* __restrict__ sq, double* __restrict__ q, int nx, int ny,
-                         int nz, double ihx2, double ihy2, double ihz2, int perx, int pery,
-                         int perz, Fd16 c) {
+__global__ void k_fd16_q(Batch b, Fields f, int nx, int ny, int nz, double ihx2, double ihy2,
+                         double ihz2, int perx, int pery, int perz, Fd16 c) {
+  SLOT_PROLOGUE(b)
+  (void)S;
+  const double* sq = f.sq + off;
+  double* q = f.q + off;
   const size_t n = (size_t)nx * ny * nz;
   GRID_STRIDE(idx, n) {
     const int i = (int)(idx % nx);
@@ -80,171 +140,6 @@ __global__ void k_fd16_q(const double* __restrict__ sq, double* __restrict__ q, 
   }
 }
 
-// qlam = q + lambda0 * gamma, gamma = (eps - 1)/(eps0 - 1); partial sums of
-// eps and lambda for the periodic k = 0 kernel value.
-__global__ void k_qlam_linear(const double* __restrict__ q, const double* __restrict__ eps,
-                              double* __restrict__ qlam, size_t n, double lambda0, double inv_e0m1,
-                              double* partials, PcgScalars* sc) {
-  double acc = 0.0;
-  GRID_STRIDE(i, n) {
-    const double lam = lambda0 * (eps[i] - 1.0) * inv_e0m1;
-    qlam[i] = q[i] + lam;
-    acc += lam;
-  }
-  grid_reduce(acc, partials, &sc->counter[CNT_AUX], &sc->aux[1]);
-}
-
-__global__ void k_sum(const double* __restrict__ a, size_t n, double* partials, unsigned int* counter,
-                      double* out) {
-  double acc = 0.0;
-  GRID_STRIDE(i, n) acc += a[i];
-  grid_reduce(acc, partials, counter, out);
-}
-
-__global__ void k_copy_scaled(const double* __restrict__ a, double* __restrict__ b, size_t n,
-                              double f) {
-  GRID_STRIDE(i, n) b[i] = f * a[i];
-}
-
-__global__ void k_mul(const double* __restrict__ a, const double* __restrict__ b,
-                      double* __restrict__ c, size_t n) {
-  GRID_STRIDE(i, n) c[i] = a[i] * b[i];
-}
-
-// ---------------------------------------------------------------- PCG ------
-
-// r_0 = -4 pi (rho - background), phi = p = A p = 0 (Algorithm 2, phi_0 = 0).
-__global__ void k_init(const double* __restrict__ rho, double* __restrict__ r,
-                       double* __restrict__ phi, double* __restrict__ p, double* __restrict__ Ap,
-                       size_t n, double tol_abs, double tol_rel, int max_iter, double* partials,
-                       PcgScalars* sc, int zero_phi, const double* bg_sum) {
-  const double bg = bg_sum ? *bg_sum / (double)n : 0.0;
-  double acc = 0.0;
-  GRID_STRIDE(i, n) {
-    const double ri = -kFourPi * (rho[i] - bg);
-    r[i] = ri;
-    if (zero_phi) phi[i] = 0.0;
-    p[i] = 0.0;
-    Ap[i] = 0.0;
-    acc += ri * ri;
-  }
-  if (grid_reduce(acc, partials, &sc->counter[CNT_RR], &sc->rr0) && threadIdx.x == 0) {
-    const double r0 = sqrt(sc->rr0);
-    const double tol = fmax(tol_abs, tol_rel * r0);
-    sc->tol2 = tol * tol;
-    sc->rr = sc->rr0;
-    sc->iter = 0;
-    sc->max_iter = max_iter;
-    sc->status = 0;
-    sc->done = (sc->rr0 <= sc->tol2) ? 1 : 0;
-    sc->vr_prev = 1.0;
-    sc->background = bg;
-  }
-}
-
-// p = v + beta p ; A p = -(q + lambda) v - 4 pi r [+ 4 pi <s r> sqrt(eps)] + beta A p ;
-// partial (p, A p).  beta = (v,r)/(v,r)_prev, beta_0 = 0 (Algorithm 2).
-// Periodic GPe (project != 0): v is first put back on the gauge subspace
-// sum sqrt(eps) v = 0 by v -= c s, c = <sqrt(eps) v>, and (v, r) is corrected
-// by -c (s, r); in exact arithmetic c = 0 (the vacuum solve drops k = 0), the
-// projection only removes the rounding of the spectrum passes.
-__global__ void k_update_p(const double* __restrict__ v, const double* __restrict__ r,
-                           const double* __restrict__ qlam, const double* __restrict__ sqrt_eps,
-                           const double* __restrict__ s, double* __restrict__ p,
-                           double* __restrict__ Ap, size_t n, double inv_n, int periodic,
-                           int project, double* partials, PcgScalars* sc) {
-  if (sc->done) return;
-  const double c = project ? sc->wsum * inv_n : 0.0;
-  const double vr = project ? sc->vr - c * sc->mu_sum : sc->vr;
-  const double beta = sc->iter == 0 ? 0.0 : vr / sc->vr_prev;
-  const double mu4pi = periodic ? kFourPi * sc->mu_sum * inv_n : 0.0;
-  double acc = 0.0;
-  GRID_STRIDE(i, n) {
-    const double vi = project ? v[i] - c * s[i] : v[i];
-    double av = -qlam[i] * vi - kFourPi * r[i];
-    if (periodic) av += mu4pi * sqrt_eps[i];
-    const double pi_ = vi + beta * p[i];
-    const double api = av + beta * Ap[i];
-    p[i] = pi_;
-    Ap[i] = api;
-    acc += pi_ * api;
-  }
-  if (grid_reduce(acc, partials, &sc->counter[CNT_PAP], &sc->pAp) && threadIdx.x == 0) {
-    const double pap = sc->pAp;
-    sc->beta = beta;
-    sc->vr = vr;
-    sc->vr_prev = vr;
-    if (!(pap < 0.0) || !isfinite(pap) || !isfinite(vr)) {
-      sc->status = GPS_ERR_BREAKDOWN;
-      sc->done = 1;
-      sc->alpha = 0.0;
-    } else {
-      sc->alpha = vr / pap;
-    }
-  }
-}
-
-// phi += alpha p ; r -= alpha A p ; partial ||r||^2 ; convergence test.
-__global__ void k_update_r(double* __restrict__ phi, double* __restrict__ r,
-                           const double* __restrict__ p, const double* __restrict__ Ap, size_t n,
-                           double* partials, PcgScalars* sc) {
-  if (sc->done) return;
-  const double alpha = sc->alpha;
-  double acc = 0.0;
-  GRID_STRIDE(i, n) {
-    phi[i] += alpha * p[i];
-    const double ri = r[i] - alpha * Ap[i];
-    r[i] = ri;
-    acc += ri * ri;
-  }
-  if (grid_reduce(acc, partials, &sc->counter[CNT_RR], &sc->rr) && threadIdx.x == 0) {
-    sc->iter += 1;
-    if (!isfinite(sc->rr)) {
-      sc->status = GPS_ERR_BREAKDOWN;
-      sc->done = 1;
-    } else if (sc->rr <= sc->tol2) {
-      sc->done = 1;
-    } else if (sc->iter >= sc->max_iter) {
-      sc->status = GPS_ERR_NOT_CONVERGED;
-      sc->done = 1;
-    }
-  }
-}
-
-// ----------------------------------------------------------- certificate --
-
-// out = rho - bg [+ rions] - qlam phi / 4 pi ; partial of sqrt(eps) phi.
-__global__ void k_fp_source(const double* __restrict__ rho, const double* __restrict__ rions,
-                            const double* __restrict__ qlam, const double* __restrict__ phi,
-                            const double* __restrict__ sq, double* __restrict__ out, size_t n,
-                            double bg, double* partials, PcgScalars* sc) {
-  double acc = 0.0;
-  const double inv4pi = 1.0 / kFourPi;
-  GRID_STRIDE(i, n) {
-    double src = rho[i] - bg - qlam[i] * phi[i] * inv4pi;
-    if (rions) src += rions[i];
-    out[i] = src;
-    acc += sq[i] * phi[i];
-  }
-  grid_reduce(acc, partials, &sc->counter[CNT_AUX], &sc->aux[5]);
-}
-
-// g = w + c s - phi ; partials of ||g||^2 (aux[6]) and ||phi||^2 (aux[7]).
-__global__ void k_fp_residual(const double* __restrict__ w, const double* __restrict__ s,
-                              const double* __restrict__ phi, size_t n, double c, double* partials,
-                              double* partials2, PcgScalars* sc) {
-  double a = 0.0, b = 0.0;
-  GRID_STRIDE(i, n) {
-    const double g = w[i] + c * s[i] - phi[i];
-    a += g * g;
-    b += phi[i] * phi[i];
-  }
-  grid_reduce(a, partials, &sc->counter[CNT_AUX], &sc->aux[6]);
-  grid_reduce(b, partials2, &sc->counter[CNT_AUX2], &sc->aux[7]);
-}
-
-// ------------------------------------------------------------------ ions ---
-
 __device__ __forceinline__ void ion_terms(double phi, double gamma, const IonParams& ip,
                                           double* rho_i, double* drho) {
   double a = 0.0, d = 0.0;
@@ -259,6 +154,341 @@ __device__ __forceinline__ void ion_terms(double phi, double gamma, const IonPar
   *drho = gamma * d;
 }
 
+// qlam = q (+ lambda0 gamma for linear PB); sums of lambda and rho.
+// Nonlinear PB also starts Algorithm 4: phi = 0, rho_ions = rho_ions[0], r' = rho.
+__global__ void k_setup_final(Batch b, Fields f, size_t n) {
+  SLOT_PROLOGUE(b)
+  const double* q = f.q + off;
+  const double* eps = f.eps + off;
+  const double* rho = f.rho + off;
+  double* qlam = f.qlam + off;
+  const int kind = S.kind;
+  const IonParams ip = S.ion;
+  double lam_acc = 0.0, rho_acc = 0.0;
+  GRID_STRIDE(i, n) {
+    double lam = 0.0;
+    if (kind == GPS_LPB) lam = ip.lambda0 * (eps[i] - 1.0) * ip.inv_eps0m1;
+    qlam[i] = q[i] + lam;
+    lam_acc += lam;
+    rho_acc += rho[i];
+    if (kind == GPS_NLPB) {
+      double a, d;
+      ion_terms(0.0, (eps[i] - 1.0) * ip.inv_eps0m1, ip, &a, &d);
+      f.phi[off + i] = 0.0;
+      f.rions[off + i] = a;
+      f.rp[off + i] = rho[i];
+    }
+  }
+  grid_reduce(lam_acc, slot_partials(b, slot), &S.counter[CNT_AUX], &S.lam_sum);
+  grid_reduce(rho_acc, slot_partials2(b, slot), &S.counter[CNT_AUX2], &S.aux[3]);
+}
+
+// Next phase after setup (one block per slot): periodic k = 0 value,
+// background and gauge, or the INVALID status for a non-positive eps.
+__global__ void k_setup_phase(Batch b, size_t n, double inv_p, int periodic) {
+  SLOT_PROLOGUE(b)
+  (void)off;
+  if (threadIdx.x != 0) return;
+  if (S.bad_eps) {
+    S.status = GPS_ERR_INVALID;
+    S.phase = PH_DONE;
+    return;
+  }
+  S.use_k0 = 0;
+  S.k0 = 0.0;
+  S.background = 0.0;
+  S.gauge = 0;
+  if (periodic && S.kind != GPS_NLPB) {
+    if (S.kind == GPS_LPB && S.lam_sum > 0) {
+      S.use_k0 = 1;
+      S.k0 = kFourPi * S.eps_sum / S.lam_sum * inv_p;
+    } else {
+      // singular operator (GPe, or linear PB without solvent): A 1 = 0 --
+      // neutral source, iterates on the gauge subspace
+      S.gauge = 1;
+      S.background = S.aux[3] / (double)n;
+    }
+  }
+  S.iters_total = 0;
+  S.fp64_iters = 0;
+  S.outer = 0;
+  S.F0 = -1.0;
+  S.F = 0.0;
+  S.cert = -1.0;
+  S.phase = S.kind == GPS_NLPB ? PH_NLEVAL : PH_INIT;
+}
+
+// ---------------------------------------------------------------- PCG ------
+
+// r_0 = -4 pi (source - background), x = p = A p = 0 (Algorithm 2, x_0 = 0);
+// source/x are rho/phi, or the inner source/correction for nonlinear PB.
+__global__ void k_init(Batch b, Fields f, size_t n) {
+  SLOT_PROLOGUE(b)
+  const bool nl = S.kind == GPS_NLPB;
+  const double* src = (nl ? f.src : f.rho) + off;
+  double* x = (nl ? f.dphi : f.phi) + off;
+  double* r = f.r + off;
+  double* p = f.p + off;
+  double* Ap = f.Ap + off;
+  const double bg = S.background;
+  double acc = 0.0;
+  GRID_STRIDE(i, n) {
+    const double ri = -kFourPi * (src[i] - bg);
+    r[i] = ri;
+    x[i] = 0.0;
+    p[i] = 0.0;
+    Ap[i] = 0.0;
+    acc += ri * ri;
+  }
+  if (grid_reduce(acc, slot_partials(b, slot), &S.counter[CNT_RR], &S.rr0) && threadIdx.x == 0) {
+    const double r0 = sqrt(S.rr0);
+    const double tol = fmax(S.tol_abs, S.tol_rel * r0);
+    S.tol2 = tol * tol;
+    S.rr = S.rr0;
+    S.iter = 0;
+    S.status = GPS_OK;
+    S.vr_prev = 1.0;
+    S.restart = 0;
+    S.spec = S.spec_hi;
+    if (S.rr0 <= S.tol2) after_pcg(S);
+    else S.phase = PH_ITER;
+  }
+}
+
+// p = v + beta p ; A p = -(q + lambda) v - 4 pi r [+ 4 pi <s r> sqrt(eps)] + beta A p ;
+// partial (p, A p).  beta = (v,r)/(v,r)_prev, beta_0 = 0 (Algorithm 2).
+// Periodic GPe (gauge): the operator is singular with A 1 = 0, so v is put
+// back on the subspace sum sqrt(eps) v = 0 (v -= c s, c = <sqrt(eps) v>, with
+// (v, r) corrected by -c (s, r)), and A p on the range of A (its grid mean m
+// is removed: alpha uses (p, A p) - m sum p and the r update uses A p - m).
+// Both are identities in exact arithmetic that remove the rounding of the
+// spectrum passes, which would otherwise leave r a component along the
+// constants that no iteration can reduce.  A breakdown while the FP32
+// spectrum is in use falls back to the FP64-accurate spectrum and restarts
+// the directions (beta = 0) instead of stopping.
+__global__ void k_update_p(Batch b, Fields f, size_t n, double inv_n, int periodic) {
+  SLOT_PROLOGUE(b)
+  const double* v = f.v + off;
+  const double* r = f.r + off;
+  const double* qlam = f.qlam + off;
+  const double* sqe = f.sq + off;
+  const double* s = f.s + off;
+  double* p = f.p + off;
+  double* Ap = f.Ap + off;
+  const bool project = S.gauge != 0;
+  const double c = project ? S.wsum * inv_n : 0.0;
+  const double vr = project ? S.vr - c * S.mu_sum : S.vr;
+  const double beta = (S.iter == 0 || S.restart) ? 0.0 : vr / S.vr_prev;
+  const double mu4pi = periodic ? kFourPi * S.mu_sum * inv_n : 0.0;
+  double acc = 0.0, ap_acc = 0.0, p_acc = 0.0;
+  GRID_STRIDE(i, n) {
+    const double vi = project ? v[i] - c * s[i] : v[i];
+    double av = -qlam[i] * vi - kFourPi * r[i];
+    if (periodic) av += mu4pi * sqe[i];
+    const double pi_ = vi + beta * p[i];
+    const double api = av + beta * Ap[i];
+    p[i] = pi_;
+    Ap[i] = api;
+    acc += pi_ * api;
+    ap_acc += api;
+    p_acc += pi_;
+  }
+  bool last;
+  if (project)
+    last = grid_reduce3(acc, ap_acc, p_acc, slot_partials(b, slot), slot_partials2(b, slot),
+                        slot_partials3(b, slot), &S.counter[CNT_PAP], &S.pAp, &S.ap_sum, &S.p_sum);
+  else
+    last = grid_reduce(acc, slot_partials(b, slot), &S.counter[CNT_PAP], &S.pAp);
+  if (last && threadIdx.x == 0) {
+    double pap = S.pAp;
+    S.ap_mean = 0.0;
+    if (project) {
+      S.ap_mean = S.ap_sum * inv_n;
+      pap -= S.ap_mean * S.p_sum;
+      S.pAp = pap;
+    }
+    S.beta = beta;
+    S.vr = vr;
+    S.vr_prev = vr;
+    S.restart = 0;
+    if (!(pap < 0.0) || !isfinite(pap) || !isfinite(vr)) {
+      S.alpha = 0.0;
+      if (S.spec == SPEC_FP32) {   // FP32 noise floor reached: continue in FP64 accuracy
+        S.spec = S.spec_hi;
+        S.mixed = 0;
+        S.restart = 1;
+      } else {
+        S.status = GPS_ERR_BREAKDOWN;
+      }
+    } else {
+      S.alpha = vr / pap;
+    }
+  }
+}
+
+// x += alpha p ; r -= alpha A p ; partial ||r||^2 ; convergence test.
+__global__ void k_update_r(Batch b, Fields f, size_t n) {
+  SLOT_PROLOGUE(b)
+  const bool nl = S.kind == GPS_NLPB;
+  double* x = (nl ? f.dphi : f.phi) + off;
+  double* r = f.r + off;
+  const double* p = f.p + off;
+  const double* Ap = f.Ap + off;
+  const double alpha = S.alpha;
+  const double m = S.gauge ? S.ap_mean : 0.0;
+  double* Apw = f.Ap + off;
+  double acc = 0.0;
+  GRID_STRIDE(i, n) {
+    x[i] += alpha * p[i];
+    const double api = Ap[i] - m;
+    if (m != 0.0) Apw[i] = api;   // keep the projected A p for the recurrence
+    const double ri = r[i] - alpha * api;
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  if (grid_reduce(acc, slot_partials(b, slot), &S.counter[CNT_RR], &S.rr) && threadIdx.x == 0) {
+    S.iter += 1;
+    S.iters_total += 1;
+    if (S.spec != SPEC_FP32) S.fp64_iters += 1;
+    if (S.status == GPS_ERR_BREAKDOWN || !isfinite(S.rr)) {
+      S.status = GPS_ERR_BREAKDOWN;
+      after_pcg(S);
+    } else if (S.rr <= S.tol2) {
+      after_pcg(S);
+    } else if (S.iter >= S.max_iter) {
+      S.status = GPS_ERR_NOT_CONVERGED;
+      after_pcg(S);
+    } else if (S.mixed && S.spec != SPEC_FP32 && S.rr <= S.mixed_switch * S.mixed_switch * S.rr0) {
+      S.spec = SPEC_FP32;
+      S.rr_min = S.rr;
+      S.stall = 0;
+    } else if (S.spec == SPEC_FP32) {
+      // The FP32 spectrum has a noise floor: once the residual stops reaching
+      // new minima, continue in FP64 with restarted directions.
+      if (S.rr < S.rr_min) {
+        S.rr_min = S.rr;
+        S.stall = 0;
+      } else if (++S.stall >= 8) {
+        S.spec = S.spec_hi;
+        S.mixed = 0;
+        S.restart = 1;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ ions ---
+
+// Outer step of Algorithm 4: fresh = rho_ions[phi]; lambda (Newton: the
+// linear PB term at phi, else 0); source = r' + mix - rho_ions, qlam = q +
+// lambda; outer residual ||fresh - rho_ions + r'||.
+__global__ void k_nl_eval(Batch b, Fields f, size_t n, double inv_p, int periodic) {
+  SLOT_PROLOGUE(b)
+  const IonParams ip = S.ion;
+  const double eta = S.newton ? 1.0 : S.eta;
+  double acc = 0.0, lam_acc = 0.0, src_acc = 0.0;
+  GRID_STRIDE(i, n) {
+    const size_t k = off + i;
+    double a, d;
+    ion_terms(f.phi[k], (f.eps[k] - 1.0) * ip.inv_eps0m1, ip, &a, &d);
+    const double lam = S.newton ? -kFourPi * d : 0.0;
+    const double ri = f.rions[k], rp = f.rp[k];
+    f.fresh[k] = a;
+    f.lam[k] = lam;
+    const double mix = eta * a + (1.0 - eta) * ri;
+    const double src = rp + mix - ri;
+    f.src[k] = src;
+    f.qlam[k] = f.q[k] + lam;
+    const double fr = a - ri + rp;
+    acc += fr * fr;
+    lam_acc += lam;
+    src_acc += src;
+  }
+  grid_reduce(lam_acc, slot_partials2(b, slot), &S.counter[CNT_AUX2], &S.lam_sum);
+  grid_reduce(src_acc, slot_partials3(b, slot), &S.counter[CNT_PSUM], &S.aux[4]);
+  if (grid_reduce(acc, slot_partials(b, slot), &S.counter[CNT_AUX], &S.aux[0]) && threadIdx.x == 0) {
+    const double F = sqrt(S.aux[0]);
+    S.F = F;
+    if (S.F0 < 0) S.F0 = F;
+    if (!isfinite(F)) {
+      S.status = GPS_ERR_BREAKDOWN;
+      S.phase = PH_DONE;
+    } else if (F <= S.tol_outer) {
+      S.status = GPS_OK;
+      S.background = 0.0;
+      S.phase = S.certify ? PH_CERT : PH_DONE;
+    } else if (S.outer >= S.max_outer) {
+      S.status = GPS_ERR_NOT_CONVERGED;
+      S.phase = PH_DONE;
+    } else {
+      if (S.newton) {
+        S.tol_abs = 0.1 * kFourPi * S.tol_outer;
+        S.tol_rel = fmin(S.forcing, F / S.F0);
+      } else if (S.outer < 2) {
+        S.tol_abs = 0.0;
+        S.tol_rel = 1e-4;
+      } else {
+        S.tol_abs = kFourPi * S.tol_outer;
+        S.tol_rel = 0.0;
+      }
+      S.use_k0 = 0;
+      S.k0 = 0.0;
+      S.gauge = 0;
+      S.background = 0.0;
+      if (periodic && S.lam_sum > 0) {
+        S.use_k0 = 1;
+        S.k0 = kFourPi * S.eps_sum / S.lam_sum * inv_p;
+      } else if (periodic) {
+        // no screening this step: singular inner operator, neutral source
+        S.gauge = 1;
+        S.background = S.aux[4] / (double)n;
+      }
+      S.phase = PH_INIT;
+    }
+  }
+}
+
+// Trial (commit == 0) or accepted (commit == 1) step t of the outer loop:
+//   phi_t = phi + t dphi ; rions_t = rions + t (mix - rions - lam dphi / 4pi) ;
+//   rp_t = (1-t) rp + t (-r / 4pi) ; F_t = ||rho_ions[phi_t] - rions_t + rp_t||.
+__global__ void k_nl_step(Batch b, Fields f, size_t n, int commit) {
+  SLOT_PROLOGUE(b)
+  const IonParams ip = S.ion;
+  const double eta = S.newton ? 1.0 : S.eta;
+  const double t = S.t;
+  const double inv4pi = 1.0 / kFourPi;
+  double acc = 0.0;
+  GRID_STRIDE(i, n) {
+    const size_t k = off + i;
+    const double ri = f.rions[k];
+    const double mix = eta * f.fresh[k] + (1.0 - eta) * ri;
+    const double dph = f.dphi[k];
+    const double ph = f.phi[k] + t * dph;
+    const double rit = ri + t * (mix - ri - f.lam[k] * dph * inv4pi);
+    const double rpt = (1.0 - t) * f.rp[k] + t * (-f.r[k] * inv4pi);
+    if (commit) {
+      f.phi[k] = ph;
+      f.rions[k] = rit;
+      f.rp[k] = rpt;
+    } else {
+      double a, d;
+      ion_terms(ph, (f.eps[k] - 1.0) * ip.inv_eps0m1, ip, &a, &d);
+      const double fr = a - rit + rpt;
+      acc += fr * fr;
+    }
+  }
+  if (grid_reduce(acc, slot_partials(b, slot), &S.counter[CNT_AUX3], &S.aux[2]) && threadIdx.x == 0) {
+    if (commit) {
+      S.outer += 1;
+      S.phase = PH_NLEVAL;
+    } else if (sqrt(S.aux[2]) < S.F || S.t < 1e-4) {
+      S.phase = PH_COMMIT;
+    } else {
+      S.t *= 0.5;
+    }
+  }
+}
+
 __global__ void k_ionic_charge(const double* __restrict__ phi, const double* __restrict__ eps,
                                double* __restrict__ out, size_t n, IonParams ip) {
   GRID_STRIDE(i, n) {
@@ -268,71 +498,49 @@ __global__ void k_ionic_charge(const double* __restrict__ phi, const double* __r
   }
 }
 
-// fresh = rho_ions[phi]; lam = -4 pi d rho_ions/d phi (newton) ; partial of
-// ||fresh - rions + rp||^2 (the outer residual).
-__global__ void k_nl_eval(const double* __restrict__ phi, const double* __restrict__ eps,
-                          const double* __restrict__ rions, const double* __restrict__ rp,
-                          double* __restrict__ fresh, double* __restrict__ lam, size_t n,
-                          IonParams ip, int newton, double* partials, PcgScalars* sc) {
-  double acc = 0.0;
-  GRID_STRIDE(i, n) {
-    double a, d;
-    ion_terms(phi[i], (eps[i] - 1.0) * ip.inv_eps0m1, ip, &a, &d);
-    fresh[i] = a;
-    lam[i] = newton ? -kFourPi * d : 0.0;
-    const double f = a - rions[i] + rp[i];
-    acc += f * f;
-  }
-  grid_reduce(acc, partials, &sc->counter[CNT_AUX], &sc->aux[0]);
-}
+// ----------------------------------------------------------- certificate --
 
-// Inner-solve inputs of one outer step: source charge and operator term.
-//   mix = eta fresh + (1-eta) rions ; src = rp + mix - rions ; qlam = q + lam.
-// Partial sums of lam (periodic k = 0 value).
-__global__ void k_nl_source(const double* __restrict__ fresh, const double* __restrict__ rions,
-                            const double* __restrict__ rp, const double* __restrict__ q,
-                            const double* __restrict__ lam, double* __restrict__ src,
-                            double* __restrict__ qlam, size_t n, double eta, double* partials,
-                            PcgScalars* sc) {
-  double acc = 0.0;
-  GRID_STRIDE(i, n) {
-    const double mix = eta * fresh[i] + (1.0 - eta) * rions[i];
-    src[i] = rp[i] + mix - rions[i];
-    qlam[i] = q[i] + lam[i];
-    acc += lam[i];
-  }
-  grid_reduce(acc, partials, &sc->counter[CNT_AUX], &sc->aux[1]);
-}
-
-// Outer residual after a trial step t (Newton line search):
-//   phi_t = phi + t dphi ; rions_t = rions + t (mix - rions - lam dphi/4pi) ;
-//   rp_t = (1-t) rp + t (-r/4pi) ;  F_t = ||rho_ions[phi_t] - rions_t + rp_t||.
-// With commit != 0 the trial state is written back.
-__global__ void k_nl_step(double* __restrict__ phi, const double* __restrict__ eps,
-                          double* __restrict__ rions, double* __restrict__ rp,
-                          const double* __restrict__ fresh, const double* __restrict__ lam,
-                          const double* __restrict__ dphi, const double* __restrict__ r, size_t n,
-                          IonParams ip, double eta, double t, int commit, double* partials,
-                          PcgScalars* sc) {
-  double acc = 0.0;
+// tmp = rho - bg [+ rho_ions[phi]] - qop phi / 4 pi, qop = q (NLPB) or
+// q + lambda ; partial of sqrt(eps) phi.
+__global__ void k_fp_source(Batch b, Fields f, size_t n) {
+  SLOT_PROLOGUE(b)
+  const bool nl = S.kind == GPS_NLPB;
+  const IonParams ip = S.ion;
+  const double bg = S.background;
   const double inv4pi = 1.0 / kFourPi;
+  double acc = 0.0;
   GRID_STRIDE(i, n) {
-    const double ri = rions[i];
-    const double mix = eta * fresh[i] + (1.0 - eta) * ri;
-    const double ph = phi[i] + t * dphi[i];
-    const double rit = ri + t * (mix - ri - lam[i] * dphi[i] * inv4pi);
-    const double rpt = (1.0 - t) * rp[i] + t * (-r[i] * inv4pi);
-    double a, d;
-    ion_terms(ph, (eps[i] - 1.0) * ip.inv_eps0m1, ip, &a, &d);
-    const double f = a - rit + rpt;
-    acc += f * f;
-    if (commit) {
-      phi[i] = ph;
-      rions[i] = rit;
-      rp[i] = rpt;
+    const size_t k = off + i;
+    const double ph = f.phi[k];
+    double src = f.rho[k] - bg - (nl ? f.q[k] : f.qlam[k]) * ph * inv4pi;
+    if (nl) {
+      double a, d;
+      ion_terms(ph, (f.eps[k] - 1.0) * ip.inv_eps0m1, ip, &a, &d);
+      src += a;
     }
+    f.tmp[k] = src;
+    acc += f.sq[k] * ph;
   }
-  grid_reduce(acc, partials, &sc->counter[CNT_AUX2], &sc->aux[2]);
+  grid_reduce(acc, slot_partials(b, slot), &S.counter[CNT_AUX], &S.aux[5]);
+}
+
+// g = w + c s - phi (w = M tmp, written into f.Ap) ; ||g|| / ||phi|| -> cert ; DONE.
+__global__ void k_fp_residual(Batch b, Fields f, size_t n, int periodic) {
+  SLOT_PROLOGUE(b)
+  const double c = periodic ? S.aux[5] / (double)n : 0.0;
+  double a = 0.0, q2 = 0.0;
+  GRID_STRIDE(i, n) {
+    const size_t k = off + i;
+    const double g = f.Ap[k] + c * f.s[k] - f.phi[k];
+    a += g * g;
+    q2 += f.phi[k] * f.phi[k];
+  }
+  grid_reduce(q2, slot_partials2(b, slot), &S.counter[CNT_AUX2], &S.aux[7]);
+  if (grid_reduce(a, slot_partials(b, slot), &S.counter[CNT_AUX], &S.aux[6]) && threadIdx.x == 0) {
+    const double nphi = sqrt(S.aux[7]);
+    S.cert = nphi > 0 ? sqrt(S.aux[6]) / nphi : sqrt(S.aux[6]);
+    S.phase = PH_DONE;
+  }
 }
 
 // ----------------------------------------------------------------- tables --
@@ -416,106 +624,73 @@ __global__ void k_axis_matrix(const double* __restrict__ in, double* __restrict_
 
 // ------------------------------------------------------------- launchers --
 
-void launch_setup_s(const double* eps, double* s, double* sq, size_t n, PcgScalars* sc,
-                    cudaStream_t st) {
+#define VEC_GRID(n, nslots) dim3(vec_blocks(n, nslots), 1, nslots), kT, 0, st
+
+void launch_setup_s(const Batch& b, const Fields& f, size_t n, int nslots, cudaStream_t st) {
   count_launch();
-  k_setup_s<<<grid_blocks(n, kT), kT, 0, st>>>(eps, s, sq, n, sc);
+  k_setup_s<<<VEC_GRID(n, nslots)>>>(b, f, n);
 }
 
-void launch_fd16_q(const double* sq, double* q, int nx, int ny, int nz, double hx, double hy,
-                   double hz, int perx, int pery, int perz, const Fd16& c, cudaStream_t st) {
+void launch_fd16_q(const Batch& b, const Fields& f, int nx, int ny, int nz, double hx, double hy,
+                   double hz, int perx, int pery, int perz, const Fd16& c, int nslots,
+                   cudaStream_t st) {
   const size_t n = (size_t)nx * ny * nz;
   count_launch();
-  k_fd16_q<<<grid_blocks(n, kT), kT, 0, st>>>(sq, q, nx, ny, nz, 1.0 / (hx * hx), 1.0 / (hy * hy),
-                                              1.0 / (hz * hz), perx, pery, perz, c);
+  k_fd16_q<<<VEC_GRID(n, nslots)>>>(b, f, nx, ny, nz, 1.0 / (hx * hx), 1.0 / (hy * hy),
+                                     1.0 / (hz * hz), perx, pery, perz, c);
 }
 
-void launch_qlam_linear(const double* q, const double* eps, double* qlam, size_t n, double lambda0,
-                        double inv_e0m1, double* partials, PcgScalars* sc, cudaStream_t st) {
+void launch_setup_final(const Batch& b, const Fields& f, size_t n, double inv_p, int periodic,
+                        int nslots, cudaStream_t st) {
   count_launch();
-  k_qlam_linear<<<grid_blocks(n, kT), kT, 0, st>>>(q, eps, qlam, n, lambda0, inv_e0m1, partials, sc);
+  k_setup_final<<<VEC_GRID(n, nslots)>>>(b, f, n);
+  count_launch();
+  k_setup_phase<<<dim3(1, 1, nslots), 32, 0, st>>>(b, n, inv_p, periodic);
 }
 
-void launch_sum(const double* a, size_t n, double* partials, unsigned int* counter, double* out,
-                cudaStream_t st) {
+void launch_init(const Batch& b, const Fields& f, size_t n, int nslots, cudaStream_t st) {
   count_launch();
-  k_sum<<<grid_blocks(n, kT), kT, 0, st>>>(a, n, partials, counter, out);
+  k_init<<<VEC_GRID(n, nslots)>>>(b, f, n);
 }
 
-void launch_copy_scaled(const double* a, double* b, size_t n, double f, cudaStream_t st) {
+void launch_update_p(const Batch& b, const Fields& f, size_t n, int periodic, int nslots,
+                     cudaStream_t st) {
   count_launch();
-  k_copy_scaled<<<grid_blocks(n, kT), kT, 0, st>>>(a, b, n, f);
+  k_update_p<<<VEC_GRID(n, nslots)>>>(b, f, n, 1.0 / (double)n, periodic);
 }
 
-void launch_mul(const double* a, const double* b, double* c, size_t n, cudaStream_t st) {
+void launch_update_r(const Batch& b, const Fields& f, size_t n, int nslots, cudaStream_t st) {
   count_launch();
-  k_mul<<<grid_blocks(n, kT), kT, 0, st>>>(a, b, c, n);
+  k_update_r<<<VEC_GRID(n, nslots)>>>(b, f, n);
 }
 
-void launch_init(const double* rho, double* r, double* phi, double* p, double* Ap, size_t n,
-                 double tol_abs, double tol_rel, int max_iter, double* partials, PcgScalars* sc,
-                 int zero_phi, const double* bg_sum, cudaStream_t st) {
+void launch_nl_eval(const Batch& b, const Fields& f, size_t n, double inv_p, int periodic,
+                    int nslots, cudaStream_t st) {
   count_launch();
-  k_init<<<grid_blocks(n, kT), kT, 0, st>>>(rho, r, phi, p, Ap, n, tol_abs, tol_rel, max_iter,
-                                            partials, sc, zero_phi, bg_sum);
+  k_nl_eval<<<VEC_GRID(n, nslots)>>>(b, f, n, inv_p, periodic);
 }
 
-void launch_update_p(const double* v, const double* r, const double* qlam, const double* sqrt_eps,
-                     const double* s, double* p, double* Ap, size_t n, int periodic, int project,
-                     double* partials, PcgScalars* sc, cudaStream_t st) {
+void launch_nl_step(const Batch& b, const Fields& f, size_t n, int commit, int nslots,
+                    cudaStream_t st) {
   count_launch();
-  k_update_p<<<grid_blocks(n, kT), kT, 0, st>>>(v, r, qlam, sqrt_eps, s, p, Ap, n, 1.0 / (double)n,
-                                                periodic, project, partials, sc);
+  k_nl_step<<<VEC_GRID(n, nslots)>>>(b, f, n, commit);
 }
 
-void launch_update_r(double* phi, double* r, const double* p, const double* Ap, size_t n,
-                     double* partials, PcgScalars* sc, cudaStream_t st) {
+void launch_fp_source(const Batch& b, const Fields& f, size_t n, int nslots, cudaStream_t st) {
   count_launch();
-  k_update_r<<<grid_blocks(n, kT), kT, 0, st>>>(phi, r, p, Ap, n, partials, sc);
+  k_fp_source<<<VEC_GRID(n, nslots)>>>(b, f, n);
 }
 
-void launch_fp_source(const double* rho, const double* rions, const double* qlam, const double* phi,
-                      const double* sq, double* out, size_t n, double bg, double* partials,
-                      PcgScalars* sc, cudaStream_t st) {
+void launch_fp_residual(const Batch& b, const Fields& f, size_t n, int periodic, int nslots,
+                        cudaStream_t st) {
   count_launch();
-  k_fp_source<<<grid_blocks(n, kT), kT, 0, st>>>(rho, rions, qlam, phi, sq, out, n, bg, partials, sc);
-}
-
-void launch_fp_residual(const double* w, const double* s, const double* phi, size_t n, double c,
-                        double* partials, double* partials2, PcgScalars* sc, cudaStream_t st) {
-  count_launch();
-  k_fp_residual<<<grid_blocks(n, kT), kT, 0, st>>>(w, s, phi, n, c, partials, partials2, sc);
+  k_fp_residual<<<VEC_GRID(n, nslots)>>>(b, f, n, periodic);
 }
 
 void launch_ionic_charge(const double* phi, const double* eps, double* out, size_t n,
                          const IonParams& ip, cudaStream_t st) {
   count_launch();
   k_ionic_charge<<<grid_blocks(n, kT), kT, 0, st>>>(phi, eps, out, n, ip);
-}
-
-void launch_nl_eval(const double* phi, const double* eps, const double* rions, const double* rp,
-                    double* fresh, double* lam, size_t n, const IonParams& ip, int newton,
-                    double* partials, PcgScalars* sc, cudaStream_t st) {
-  count_launch();
-  k_nl_eval<<<grid_blocks(n, kT), kT, 0, st>>>(phi, eps, rions, rp, fresh, lam, n, ip, newton,
-                                               partials, sc);
-}
-
-void launch_nl_source(const double* fresh, const double* rions, const double* rp, const double* q,
-                      const double* lam, double* src, double* qlam, size_t n, double eta,
-                      double* partials, PcgScalars* sc, cudaStream_t st) {
-  count_launch();
-  k_nl_source<<<grid_blocks(n, kT), kT, 0, st>>>(fresh, rions, rp, q, lam, src, qlam, n, eta,
-                                                 partials, sc);
-}
-
-void launch_nl_step(double* phi, const double* eps, double* rions, double* rp, const double* fresh,
-                    const double* lam, const double* dphi, const double* r, size_t n,
-                    const IonParams& ip, double eta, double t, int commit, double* partials,
-                    PcgScalars* sc, cudaStream_t st) {
-  count_launch();
-  k_nl_step<<<grid_blocks(n, kT), kT, 0, st>>>(phi, eps, rions, rp, fresh, lam, dphi, r, n, ip, eta,
-                                               t, commit, partials, sc);
 }
 
 void launch_table_periodic(double* kern, double* lap, int Hx, int hy, int hz, double dkx, double dky,

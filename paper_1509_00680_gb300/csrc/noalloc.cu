@@ -143,12 +143,17 @@ extern "C" int gps_vacuum_solve_noalloc(const gps_grid* grid, const double* sigm
   g.lines_x = lines_per_block(Px, (g.nrows + 1) / 2);
   g.tile_y = lines_per_block(Py, Hx * grid->nz);
   g.tile_z = lines_per_block(Pz, Hx * Py);
-  launch_x_fwd<double2>(g, sx, twx, sigma_dev, nullptr, W, nullptr, st);
-  launch_y<double2>(g, sy, twy, W, false, nullptr, st);
-  launch_z<double2>(g, sz, twz, W, table, 0.0, 0, nullptr, nullptr, st);
-  launch_y<double2>(g, sy, twy, W, true, nullptr, st);
-  launch_x_inv<double2>(g, sx, twx, W, w_dev, nullptr, nullptr, nullptr, nullptr, 0, nullptr,
-                        nullptr, st);
+  Batch b{};                 // one slot, no phase machine
+  PipeArgs a{};
+  a.in = sigma_dev;
+  a.out = w_dev;
+  a.table = table;
+  a.W = W;
+  launch_x_fwd<double2>(g, sx, twx, b, a, 1, st);
+  launch_y<double2>(g, sy, twy, b, a, false, 1, st);
+  launch_z<double2>(g, sz, twz, b, a, 1, st);
+  launch_y<double2>(g, sy, twy, b, a, true, 1, st);
+  launch_x_inv<double2>(g, sx, twx, b, a, 1, st);
   if (cudaGetLastError() != cudaSuccess) return GPS_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return GPS_ERR_CUDA;
   return GPS_OK;

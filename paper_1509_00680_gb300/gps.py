@@ -16,7 +16,7 @@ from .build import LIB
 GPS_OK, GPS_ERR_INVALID, GPS_ERR_NOMEM, GPS_ERR_NOT_CONVERGED = 0, 1, 2, 3
 GPS_ERR_BREAKDOWN, GPS_ERR_TIMEOUT, GPS_ERR_CUDA, GPS_PENDING = 4, 5, 6, 7
 GPS_BC_FREE, GPS_BC_PERIODIC, GPS_BC_SURFACE = 0, 1, 2
-GPS_FP64, GPS_MIXED = 0, 1
+GPS_FP64, GPS_MIXED, GPS_DF64, GPS_MIXED_DF64 = 0, 1, 2, 3
 GPS_GPE, GPS_LPB, GPS_NLPB = 0, 1, 2
 GPS_OUTER_NEWTON, GPS_OUTER_PRINTED = 0, 1
 GPS_MAX_SPECIES = 8
@@ -54,6 +54,12 @@ class gps_report(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gps_request(ctypes.Structure):
+    _fields_ = [("grid", gps_grid), ("kind", ctypes.c_int), ("el", gps_electrolyte),
+                ("opts", gps_opts), ("rho_host", ctypes.c_void_p), ("eps_host", ctypes.c_void_p),
+                ("phi_host", ctypes.c_void_p)]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "gps_default_opts": (None, [ctypes.POINTER(gps_opts)]),
@@ -77,6 +83,14 @@ _SIGS = {
     "gps_ionic_charge": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P,
                                         ctypes.POINTER(gps_electrolyte), _P, _P]),
     "gps_vacuum_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(gps_grid), _P, _P, _P]),
+    "gps_batch_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(gps_request),
+                                       ctypes.POINTER(gps_report)]),
+    "gps_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_size_t, ctypes.c_int]),
+    "gps_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(gps_request), ctypes.POINTER(ctypes.c_ulonglong)]),
+    "gps_server_poll": (ctypes.c_int, [_P, ctypes.c_ulonglong, ctypes.POINTER(gps_report)]),
+    "gps_server_wait": (ctypes.c_int, [_P, ctypes.c_ulonglong, ctypes.POINTER(gps_report)]),
+    "gps_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int)]),
+    "gps_server_destroy": (None, [_P]),
     "gps_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "gps_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
@@ -232,13 +246,14 @@ class Context:
         _check(s, "gps_gpe_solve_host")
         return rep
 
-    def pb_solve_host(self, grid, rho, eps, electrolyte, kind, phi, opts=None, stream=None):
+    def pb_solve_host(self, grid, rho, eps, electrolyte, kind, phi, opts=None, stream=None,
+                      allow=(GPS_OK,)):
         rep = gps_report()
         o = opts if opts is not None else default_opts()
         s = load().gps_pb_solve_host(self.handle, ctypes.byref(grid), _host(rho), _host(eps),
                                      ctypes.byref(electrolyte), int(KIND.get(kind, kind)),
                                      _host(phi), ctypes.byref(o), ctypes.byref(rep), _stream(stream))
-        _check(s, "gps_pb_solve_host")
+        _check(s, "gps_pb_solve_host", allow)
         return rep
 
     # --- steps -----------------------------------------------------------
@@ -258,6 +273,80 @@ class Context:
         _check(load().gps_ionic_charge(self.handle, ctypes.byref(grid), _dev(phi), _dev(eps),
                                        ctypes.byref(electrolyte), _dev(out), _stream(stream)),
                "gps_ionic_charge")
+
+
+def make_request(grid, kind, rho, eps, phi, electrolyte=None, opts=None):
+    """A gps_request over host arrays (C-contiguous float64 numpy arrays that
+    must stay alive until the request completes)."""
+    r = gps_request()
+    r.grid = grid
+    r.kind = int(KIND.get(kind, kind))
+    if electrolyte is not None:
+        r.el = electrolyte
+    r.opts = opts if opts is not None else default_opts()
+    r.rho_host = _host(rho)
+    r.eps_host = _host(eps)
+    r.phi_host = _host(phi)
+    return r
+
+
+def batch_solve(ctx, requests, allow=(GPS_OK,)):
+    """Solve gps_requests together (continuous batching); returns the reports."""
+    n = len(requests)
+    arr = (gps_request * n)(*requests)
+    reps = (gps_report * n)()
+    s = load().gps_batch_solve(ctx.handle, n, arr, reps)
+    _check(s, "gps_batch_solve", allow)
+    return list(reps)
+
+
+class Server:
+    """Asynchronous serving loop (gps_server_*)."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0, max_slots=0):
+        h = ctypes.c_void_p()
+        _check(load().gps_server_create(ctypes.byref(h), int(device), int(hbm_budget_bytes),
+                                        int(max_slots)), "gps_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, request, keep=None):
+        t = ctypes.c_ulonglong()
+        _check(load().gps_server_submit(self.handle, ctypes.byref(request), ctypes.byref(t)),
+               "gps_server_submit")
+        self._keep[t.value] = (request, keep)
+        return t.value
+
+    def poll(self, ticket):
+        rep = gps_report()
+        s = load().gps_server_poll(self.handle, ctypes.c_ulonglong(ticket), ctypes.byref(rep))
+        if s == GPS_PENDING:
+            return None
+        self._keep.pop(ticket, None)
+        return s, rep
+
+    def wait(self, ticket):
+        rep = gps_report()
+        s = load().gps_server_wait(self.handle, ctypes.c_ulonglong(ticket), ctypes.byref(rep))
+        self._keep.pop(ticket, None)
+        return s, rep
+
+    def stats(self):
+        b = ctypes.c_size_t()
+        m = ctypes.c_int()
+        _check(load().gps_server_stats(self.handle, ctypes.byref(b), ctypes.byref(m)), "gps_server_stats")
+        return {"bytes_in_use": b.value, "max_concurrent": m.value}
+
+    def close(self):
+        if self.handle:
+            load().gps_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def vacuum_solve_noalloc(grid, sigma, w, stream=None):

@@ -290,29 +290,40 @@ def free_union(n=256, h=0.3, count=200, margin=10.0, kind="nlpb", conc=0.5, seed
 
 
 def serving_request(rng, edge, bc, kind, h=0.3):
-    """One serving request: cubic grid of `edge` points, 5-80 charges placed
-    by the periodic-cluster rules (free/surface keep a 3-bohr margin on free
-    faces), 1:1 electrolyte with c ~ log-U[0.01, 1] mol/L."""
-    count = int(rng.integers(5, 81))
+    """One serving request: cubic grid of `edge` points, 2-80 charges placed
+    by the periodic-cluster rules, 1:1 electrolyte with c ~ log-U[0.01, 1]
+    mol/L.  On a free axis every cavity ends 3 Delta inside the faces (the
+    sphere radius is clipped to 0.45 (n-1) h - 3 Delta in small boxes), so that eps
+    is flat across the free boundary; the spheres fill about a third of the
+    box at most, so that there is solvent around the solute."""
+    delta = 0.5
     if bc == BC_SURFACE:
         grid = Grid(edge, edge, edge, h, h, h, bc, origin=(0.0, 0.0, 0.0))
     else:
         grid = Grid(edge, edge, edge, h, h, h, bc)
     L = edge * h
+    span = (edge - 1) * h            # first to last grid point of a free axis
+    per = grid.periodic_axes()
+    dmax = 1.2 * 3.5
+    if not all(per):
+        dmax = min(dmax, 0.45 * span - 3.0 * delta)
     lo = [0.0, 0.0, 0.0]
     hi = [L, L, L]
-    per = grid.periodic_axes()
     for a in range(3):
         if not per[a]:
-            lo[a], hi[a] = 0.3 * L, 0.7 * L
-    count = max(2, min(count, int(8 * np.prod([hi[a] - lo[a] for a in range(3)]) / 65.0)))
-    pos = _place(rng, grid, count, lo, hi, 2.5)
+            lo[a], hi[a] = dmax + 3.0 * delta, span - dmax - 3.0 * delta
+    width = [hi[a] - lo[a] for a in range(3)]
+    rmean = min(1.2 * 3.0, dmax)
+    fill = int(0.35 * L ** 3 / (4.0 / 3.0 * np.pi * rmean ** 3))
+    count = int(rng.integers(5, 81))
+    count = max(2, min(count, fill, int(np.prod(width) / 25.0)))
+    pos = _place(rng, grid, count, lo, hi, min(2.5, 0.5 * min(width)))
     qs = _neutral_charges(rng, count, (-2, -1, 1, 2))
     sig = rng.uniform(0.8, 1.5, size=count)
-    radii = 1.2 * rng.uniform(2.5, 3.5, size=count)
+    radii = np.minimum(1.2 * rng.uniform(2.5, 3.5, size=count), dmax)
     charges = [(float(qs[i]), float(sig[i]), tuple(pos[i])) for i in range(count)]
     spheres = [(float(radii[i]), tuple(pos[i])) for i in range(count)]
-    eps = rigid_cavity(grid, spheres, 0.5)
+    eps = rigid_cavity(grid, spheres, delta)
     conc = float(np.exp(rng.uniform(np.log(0.01), np.log(1.0))))
     return Problem("req_%s_%d_%s" % (BC_NAMES[bc], edge, kind), grid,
                    gaussian_charges(grid, charges), eps, kind=kind,

@@ -53,15 +53,17 @@ def test_struct_layout_matches_header(tmp_path):
     from paper_1509_00680_gb300 import gps
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gps.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(gps_grid),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gps_grid),'
                     ' sizeof(gps_electrolyte), sizeof(gps_opts), sizeof(gps_report),'
-                    ' offsetof(gps_opts, precision), offsetof(gps_report, time_ms)); return 0;}\n')
+                    ' offsetof(gps_opts, precision), offsetof(gps_report, time_ms),'
+                    ' sizeof(gps_request), offsetof(gps_request, phi_host)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     want = [ctypes.sizeof(gps.gps_grid), ctypes.sizeof(gps.gps_electrolyte),
             ctypes.sizeof(gps.gps_opts), ctypes.sizeof(gps.gps_report),
-            gps.gps_opts.precision.offset, gps.gps_report.time_ms.offset]
+            gps.gps_opts.precision.offset, gps.gps_report.time_ms.offset,
+            ctypes.sizeof(gps.gps_request), gps.gps_request.phi_host.offset]
     assert [int(x) for x in out] == want
 
 

@@ -346,3 +346,55 @@ def test_fp64_certificate(gps, ctx):
     rep = ctx.gpe_solve(gps.grid_from(p2.grid), T(p2.rho), T(p2.eps), T(np.zeros(p2.grid.shape)),
                         gps.default_opts(tol_abs=0.0, tol_rel=1e-13, certify=1))
     assert 0 <= rep.fixed_point_res < 1e-12
+
+
+# ----------------------------------------------------- double-float spectrum
+
+@pytest.mark.parametrize("bc,n,h", SMALL)
+def test_precondition_df64(gps, ctx, bc, n, h):
+    """Spectrum passes in double-float (two floats, ~48 bits) on the FP32 pipe."""
+    g = _grid(bc, n, h)
+    rng = np.random.default_rng(16)
+    eps = 1.0 + 30.0 * rng.random(g.shape)
+    r = rng.standard_normal(g.shape)
+    f = Fields(g, eps)
+    v = T(np.zeros(g.shape))
+    ctx.precondition(gps.grid_from(g), T(f.s), T(r), v, precision=gps.GPS_DF64)
+    assert relmax(N(v, g.shape), f.precondition(r)) < 1e-12
+
+
+@pytest.mark.parametrize("wl,kw,kind", [
+    (1, dict(), "gpe"),
+    (2, dict(n=48, count=8), "gpe"),
+    (3, dict(nxy=32, nz=96, count=6), "lpb"),
+])
+def test_df64_solves(gps, ctx, wl, kw, kind):
+    p = synth.workload(wl, **kw)
+    if p.electrolyte is None:
+        p.electrolyte = synth.Electrolyte((1, -1), (0.3, 0.3), 300.0)
+    got, ref, rep, info = _solve_pair(gps, ctx, p, kind=kind, precision=gps.GPS_DF64)
+    assert rep.status == 0
+    assert rep.fp64_iters == rep.iters
+    assert rel2(got, ref) <= 1e-10
+
+
+def test_df64_nlpb(gps, ctx):
+    p = synth.workload(3, nxy=32, nz=64, count=8, kind="nlpb")
+    el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+    phi = T(np.zeros(p.grid.shape))
+    opts = gps.default_opts(tol_outer=1e-11, max_iter=3000, precision=gps.GPS_DF64)
+    rep = ctx.pb_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), el, "nlpb", phi, opts)
+    ref, info = oracle.solve_nlpb(p.grid, p.rho, p.eps, p.electrolyte, p.eps0, tol=1e-11, max_iter=3000)
+    assert rep.status == 0
+    assert rel2(N(phi, p.grid.shape), ref) <= 1e-9
+
+
+def test_mixed_df64(gps, ctx):
+    p = synth.workload(4, n=64, count=12, margin=6.0, kind="gpe")
+    phi = T(np.zeros(p.grid.shape))
+    opts = gps.default_opts(tol_abs=1e-10, precision=gps.GPS_MIXED_DF64, max_iter=2000)
+    rep = ctx.gpe_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), phi, opts)
+    ref, _ = oracle.solve_gpe(p.grid, p.rho, p.eps, tol_abs=0.0, tol_rel=1e-13, max_iter=2000)
+    assert rep.status == 0 and 0 < rep.fp64_iters < rep.iters
+    assert 0 <= rep.fixed_point_res < 1e-8
+    assert rel2(N(phi, p.grid.shape), ref) <= 1e-8

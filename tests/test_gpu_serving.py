@@ -1,0 +1,161 @@
+"""Batched and served solves (continuous batching over pools of slots).
+
+Each request reduces in a fixed order inside its own slot, so its potential
+must be bitwise identical whether it is solved alone (gps_pb_solve_host) or
+together with other requests of other sizes, boundary conditions, problems
+and precisions (gps_batch_solve, gps_server_*).  One request of each kind is
+also checked against the CPU oracle.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gps():
+    from paper_1509_00680_gb300 import build
+    build.build()
+    from paper_1509_00680_gb300 import gps as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(gps):
+    c = gps.Context(0)
+    yield c
+    c.close()
+
+
+def _requests(gps, count=10, seed=7):
+    """Small requests drawn like the serving workload (edges 24/32/36)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        edge = int(rng.choice([24, 32, 36]))
+        bc = int(rng.integers(0, 3))
+        kind = ("gpe", "lpb", "nlpb")[int(rng.integers(0, 3))]
+        p = synth.serving_request(rng, edge, bc, kind, h=0.45)
+        mixed = bool(rng.integers(0, 2)) and kind != "nlpb"
+        opts = gps.default_opts(tol_abs=1e-10, max_iter=2000, tol_outer=1e-10,
+                                precision=gps.GPS_MIXED if mixed else gps.GPS_FP64)
+        el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar,
+                                  p.electrolyte.temperature, p.eps0)
+        out.append((p, kind, opts, el))
+    return out
+
+
+def _alone(gps, ctx, reqs):
+    res = []
+    for p, kind, opts, el in reqs:
+        phi = np.zeros(p.grid.npts)
+        rep = ctx.pb_solve_host(gps.grid_from(p.grid), np.ascontiguousarray(p.rho.ravel()),
+                                np.ascontiguousarray(p.eps.ravel()), el, kind, phi, opts)
+        res.append((phi, rep))
+    return res
+
+
+def test_batch_identical_to_alone(gps, ctx):
+    reqs = _requests(gps)
+    alone = _alone(gps, ctx, reqs)
+    keep, rs = [], []
+    for p, kind, opts, el in reqs:
+        rho = np.ascontiguousarray(p.rho.ravel())
+        eps = np.ascontiguousarray(p.eps.ravel())
+        phi = np.full(p.grid.npts, np.nan)
+        keep.append((rho, eps, phi))
+        rs.append(gps.make_request(gps.grid_from(p.grid), kind, rho, eps, phi, el, opts))
+    reps = gps.batch_solve(ctx, rs)
+    for (phi_a, rep_a), (_, _, phi_b), rep_b in zip(alone, keep, reps):
+        assert rep_b.status == 0 and rep_a.status == 0
+        assert rep_a.iters == rep_b.iters
+        assert np.array_equal(phi_a, phi_b)
+
+
+def test_batch_against_oracle(gps, ctx):
+    g = synth.Grid(32, 32, 32, 0.45, 0.45, 0.45, synth.BC_PERIODIC)
+    rng = np.random.default_rng(3)
+    p = synth.serving_request(rng, 32, synth.BC_PERIODIC, "gpe", h=0.45)
+    q = synth.serving_request(rng, 24, synth.BC_FREE, "lpb", h=0.45)
+    keep, rs = [], []
+    for pr, kind in ((p, "gpe"), (q, "lpb")):
+        rho = np.ascontiguousarray(pr.rho.ravel())
+        eps = np.ascontiguousarray(pr.eps.ravel())
+        phi = np.zeros(pr.grid.npts)
+        keep.append(phi)
+        el = gps.make_electrolyte(pr.electrolyte.z, pr.electrolyte.c_molar, 300.0, pr.eps0)
+        rs.append(gps.make_request(gps.grid_from(pr.grid), kind, rho, eps, phi, el,
+                                   gps.default_opts(tol_abs=0.0, tol_rel=1e-13, max_iter=3000)))
+    gps.batch_solve(ctx, rs)
+    ref_p, _ = oracle.solve_gpe(p.grid, p.rho, p.eps, tol_abs=0.0, tol_rel=1e-13, max_iter=3000)
+    lam = oracle.pb.linear_lambda(oracle.pb.exclusion_from_eps(q.eps, q.eps0), q.electrolyte)
+    ref_q, _ = oracle.solve_lpb(q.grid, q.rho, q.eps, lam, tol_abs=0.0, tol_rel=1e-13, max_iter=3000)
+    for got, ref in ((keep[0], ref_p), (keep[1], ref_q)):
+        got = got.reshape(ref.shape)
+        assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_server_stream_identical_to_alone(gps, ctx):
+    reqs = _requests(gps, count=12, seed=11)
+    alone = _alone(gps, ctx, reqs)
+    srv = gps.Server(0, hbm_budget_bytes=8 << 30)
+    rng = np.random.default_rng(5)
+    tickets, keep = [], []
+
+    def producer():
+        for p, kind, opts, el in reqs:
+            rho = np.ascontiguousarray(p.rho.ravel())
+            eps = np.ascontiguousarray(p.eps.ravel())
+            phi = np.full(p.grid.npts, np.nan)
+            keep.append((rho, eps, phi))
+            r = gps.make_request(gps.grid_from(p.grid), kind, rho, eps, phi, el, opts)
+            tickets.append(srv.submit(r, keep=keep[-1]))
+            time.sleep(float(rng.exponential(0.003)))   # Poisson arrivals
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    results = [srv.wait(t) for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    for (phi_a, rep_a), (_, _, phi_b), (status, rep_b) in zip(alone, keep, results):
+        assert status == 0
+        assert rep_b.time_ms > 0
+        assert np.array_equal(phi_a, phi_b)
+    assert stats["max_concurrent"] >= 2
+
+
+def test_server_admission_under_budget(gps):
+    """A budget that holds one small pool at a time still completes every
+    request (pools are evicted when idle); a budget below one pool fails the
+    request with GPS_ERR_NOMEM instead of hanging."""
+    rng = np.random.default_rng(9)
+    a = synth.serving_request(rng, 24, synth.BC_PERIODIC, "gpe", h=0.45)
+    b = synth.serving_request(rng, 32, synth.BC_FREE, "gpe", h=0.45)
+    srv = gps.Server(0, hbm_budget_bytes=64 << 20, max_slots=2)
+    keep, tickets = [], []
+    for p in (a, b, a, b):
+        rho = np.ascontiguousarray(p.rho.ravel())
+        eps = np.ascontiguousarray(p.eps.ravel())
+        phi = np.zeros(p.grid.npts)
+        keep.append(phi)
+        tickets.append(srv.submit(gps.make_request(gps.grid_from(p.grid), "gpe", rho, eps, phi),
+                                  keep=(rho, eps, phi)))
+    out = [srv.wait(t) for t in tickets]
+    srv.close()
+    assert all(s == 0 for s, _ in out)
+    assert np.array_equal(keep[0], keep[2]) and np.array_equal(keep[1], keep[3])
+    tiny = gps.Server(0, hbm_budget_bytes=1 << 20)
+    rho = np.ascontiguousarray(a.rho.ravel())
+    eps = np.ascontiguousarray(a.eps.ravel())
+    phi = np.zeros(a.grid.npts)
+    t = tiny.submit(gps.make_request(gps.grid_from(a.grid), "gpe", rho, eps, phi), keep=(rho, eps, phi))
+    status, _ = tiny.wait(t)
+    tiny.close()
+    assert status == gps.GPS_ERR_NOMEM
