@@ -182,6 +182,7 @@ def run_ours(args, ws, rank, local):
     ctx.get_profile(reset=True)
     launches0 = gps.kernel_launches()
     t_steps, iters = [], []
+    torch.cuda.profiler.start()               # ncu --profile-from-start off: timed steps only
     for _ in range(args.steps):
         flush.fill_(1.0)                      # evict L2 between steps (not timed)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -192,6 +193,7 @@ def run_ours(args, ws, rank, local):
         e1.synchronize()
         t_steps.append(e0.elapsed_time(e1))
         iters.append(rep.iters)
+    torch.cuda.profiler.stop()
     barrier()
     launches = gps.kernel_launches() - launches0
     prof = ctx.get_profile(reset=True)
@@ -210,6 +212,8 @@ def run_ours(args, ws, rank, local):
     if not args.no_e2e:
         e2e = run_e2e(ctx, g, p, npts, opts, flush, args)
     mixed = None if args.no_mixed else run_mixed(ctx, g, rho, eps, phi, flush, args, gps, total_ms / args.steps)
+    df64 = None if args.no_mixed else run_mixed(ctx, g, rho, eps, phi, flush, args, gps, total_ms / args.steps,
+                                                precision=gps.GPS_DF64)
     serving = None if args.no_serving else run_serving(gps, local, args)
 
     # roofline of the dominant kernel (largest share of kernel time in warm-up)
@@ -231,6 +235,7 @@ def run_ours(args, ws, rank, local):
         "solves_per_s": ws * args.steps / (total_ms / 1e3),
         "e2e": e2e,
         "mixed": mixed,
+        "df64": df64,
         "serving": serving,
         "roofline": roof,
         "gpu_launches": int(launches),
@@ -246,13 +251,16 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
-def run_mixed(ctx, g, rho, eps, phi64, flush, args, gps, fp64_ms):
-    """The same workload with the FP32 spectrum inside the FP64 PCG: solves/s,
-    relative L2 error against the FP64 GPU result, FP64 certificate."""
+def run_mixed(ctx, g, rho, eps, phi64, flush, args, gps, fp64_ms, precision=None):
+    """The same workload with another spectrum precision inside the FP64 PCG
+    (default: FP32 after the switch; GPS_DF64: double-float throughout):
+    solves/s, relative L2 error against the FP64 GPU result, FP64
+    certificate."""
     import torch
     stream = torch.cuda.current_stream()
     phi = torch.empty_like(phi64)
-    o = gps.default_opts(tol_abs=1e-10, precision=gps.GPS_MIXED)
+    prec = gps.GPS_MIXED if precision is None else precision
+    o = gps.default_opts(tol_abs=1e-10, precision=prec)
     ctx.gpe_solve(g, rho, eps, phi, o)
     ms, reps = 0.0, []
     for _ in range(args.steps):
@@ -268,7 +276,8 @@ def run_mixed(ctx, g, rho, eps, phi64, flush, args, gps, fp64_ms):
     return {"solves_per_s": args.steps / (ms / 1e3), "ms_per_solve": ms / args.steps,
             "speedup_vs_fp64": fp64_ms / (ms / args.steps), "rel_l2_err_vs_fp64": err,
             "certificate": reps[-1].fixed_point_res, "pcg_iters": reps[-1].iters,
-            "fp64_iters": reps[-1].fp64_iters, "switch": 1e-2}
+            "fp64_iters": reps[-1].fp64_iters,
+            "spectrum": {gps.GPS_MIXED: "fp32 after ||r|| <= 1e-2 ||r0||", gps.GPS_DF64: "df64"}.get(prec, prec)}
 
 
 def run_serving(gps, device, args, count=None):
@@ -396,6 +405,86 @@ def run_reference(args, ws, rank):
     print(json.dumps(out))
 
 
+PASS_CASES = {
+    # name: (nx, ny, nz, bc) at h = 0.3 bohr
+    "free256": (256, 256, 256, 0),
+    "periodic128": (128, 128, 128, 1),
+    "periodic256": (256, 256, 256, 1),
+    "surface160": (160, 160, 256, 2),
+}
+
+
+def pass_bytes(P, e):
+    """Algorithmic HBM bytes of each spectrum pass of one preconditioner
+    application: FP64 input r and factor s, spectrum elements of e bytes
+    (only the planes and rows that hold data are read or written), the
+    octant table in FP64, FP64 output v and factor s."""
+    n = P["nx"] * P["ny"] * P["nz"]
+    half = P["nz"] * P["ny"] * P["Hx"] * e
+    full = P["nz"] * P["Py"] * P["Hx"] * e
+    table = P["Hx"] * (P["Py"] // 2 + 1) * (P["Pz"] // 2 + 1) * 8
+    return {"x_fwd": 16 * n + half, "y_fwd": half + full, "z": 2 * full + table,
+            "y_inv": full + half, "x_inv": half + 16 * n}
+
+
+def run_passes(args):
+    """Per-pass device time and achieved HBM GB/s of one preconditioner
+    application v = s S(s r) in each spectrum precision, with random r and s;
+    one more application per precision runs inside a profiler region for ncu
+    (--profile-from-start off)."""
+    import torch
+    from paper_1509_00680_gb300 import build
+    import synth
+    build.build()
+    from paper_1509_00680_gb300 import gps
+    nx, ny, nz, bc = PASS_CASES[args.passes]
+    origin = (0.0, 0.0, 0.0)
+    grid = synth.Grid(nx, ny, nz, 0.3, 0.3, 0.3, bc, origin=origin)
+    g = gps.grid_from(grid)
+    n = grid.npts
+    rng = np.random.default_rng(0)
+    s = torch.from_numpy(rng.uniform(0.1, 1.0, n)).cuda()
+    r = torch.from_numpy(rng.standard_normal(n)).cuda()
+    v = torch.zeros_like(r)
+    ctx = gps.Context(0)
+    P = pass_geometry(grid)
+    peak = peaks().get("hbm_gbs")
+    codes = {"fp64": (gps.GPS_FP64, 16), "fp32": (gps.GPS_MIXED, 8), "df64": (gps.GPS_DF64, 16)}
+    out = {"passes": args.passes, "grid": [nx, ny, nz], "bc": bc, "P": [P["Px"], P["Py"], P["Pz"]],
+           "hbm_peak_gbs": peak}
+    for name in args.precisions.split(","):
+        code, e = codes[name]
+        for _ in range(3):
+            ctx.precondition(g, s, r, v, code)
+        ctx.set_profiling("all")
+        ctx.get_profile(reset=True)
+        for _ in range(args.steps):
+            ctx.precondition(g, s, r, v, code)
+        torch.cuda.synchronize()
+        prof = ctx.get_profile(reset=True)
+        ctx.set_profiling(None)
+        byt = pass_bytes(P, e)
+        res, tot = {}, 0.0
+        for k, (cnt, ms) in prof.items():
+            if not cnt:
+                continue
+            t = ms / cnt
+            tot += t
+            res[k] = {"us": round(t * 1e3, 2), "bytes": byt.get(k)}
+            if k in byt:
+                res[k]["GBs"] = round(byt[k] / (t * 1e-3) / 1e9, 1)
+                if peak:
+                    res[k]["frac_hbm"] = round(byt[k] / (t * 1e-3) / 1e9 / peak, 3)
+        res["total_us"] = round(tot * 1e3, 2)
+        out[name] = res
+        torch.cuda.profiler.start()
+        ctx.precondition(g, s, r, v, code)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    print(json.dumps(out))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,7 +497,13 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--clocks-log", default=None, help="keep the nvidia-smi samples of the timed region here")
     ap.add_argument("--serving-count", type=int, default=24)
+    ap.add_argument("--passes", default=None, choices=sorted(PASS_CASES),
+                    help="per-pass times of one preconditioner application instead of the bench")
+    ap.add_argument("--precisions", default="fp64,df64,fp32")
     args = ap.parse_args()
+    if args.passes:
+        run_passes(args)
+        return
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)

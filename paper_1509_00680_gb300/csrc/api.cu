@@ -306,6 +306,8 @@ struct Shape {
   float2 *twx32 = nullptr, *twy32 = nullptr, *twz32 = nullptr;
   dfc *twxdf = nullptr, *twydf = nullptr, *twzdf = nullptr;
   double* table = nullptr;
+  float* table32 = nullptr;   // table rounded to float (FP32 spectrum)
+  float2* tabledf = nullptr;  // table as double-float (df64 spectrum)
   double* lap = nullptr;
   DevMem mem;
 };
@@ -424,6 +426,9 @@ std::shared_ptr<Shape> build_shape(const gps_grid* gr, cudaStream_t st) {
   } else {
     build_free_table(S.get(), st);
   }
+  S->table32 = S->mem.alloc<float>(tab);
+  S->tabledf = S->mem.alloc<float2>(tab);
+  launch_table_split(S->table, S->table32, S->tabledf, tab, st);
   ck(cudaStreamSynchronize(st));
   ck(cudaGetLastError());
   return S;
@@ -675,6 +680,8 @@ void tune_spec(Shape& S, cudaStream_t st) {
     a.in = in;
     a.out = outv;
     a.table = S.table;
+    a.table32 = S.table32;
+    a.tabledf = S.tabledf;
     a.W = W;
     TuneVal best;
     best.g = S.g;
@@ -771,6 +778,8 @@ void launch_round(Pool& P, int m, bool setup, bool init, cudaStream_t st) {
   it.out_scale = f.s;
   it.dot_with = f.r;
   it.table = S.table;
+  it.table32 = S.table32;
+  it.tabledf = S.tabledf;
   it.slot_k0 = 1;
   it.red_mu = periodic;
   it.red_wsum = periodic;
@@ -797,6 +806,8 @@ void launch_round(Pool& P, int m, bool setup, bool init, cudaStream_t st) {
     c.out = f.Ap;
     c.out_scale = f.s;
     c.table = S.table;
+    c.table32 = S.table32;
+    c.tabledf = S.tabledf;
     c.slot_k0 = 1;
     pipeline<double2>(P, bc, c, st);
     launch_fp_residual(bc, f, n, periodic, ns, st);
@@ -1394,6 +1405,8 @@ int gps_vacuum_solve(gps_ctx* ctx, const gps_grid* grid, const double* sigma, do
   a.in = sigma;
   a.out = w;
   a.table = P->shape->table;
+  a.table32 = P->shape->table32;
+  a.tabledf = P->shape->tabledf;
   pipeline<double2>(*P, b, a, st);
   return finish(GPS_OK, st);
   GPS_GUARD_END
@@ -1418,6 +1431,8 @@ int gps_precondition(gps_ctx* ctx, const gps_grid* grid, const double* s, const 
   a.out = v;
   a.out_scale = s;
   a.table = P->shape->table;
+  a.table32 = P->shape->table32;
+  a.tabledf = P->shape->tabledf;
   if (precision == GPS_MIXED) pipeline<float2>(*P, b, a, st);
   else if (precision == GPS_DF64) pipeline<dfc>(*P, b, a, st);
   else pipeline<double2>(*P, b, a, st);

@@ -48,6 +48,55 @@ __device__ __forceinline__ df operator*(df a, df b) {
 }
 __device__ __forceinline__ df fma(df a, df b, df c) { return a * b + c; }
 
+// IEEE 754 conversions on the integer pipe.  On this GPU the FP64 pipe,
+// which also carries the double <-> float conversion instructions, issues at
+// 1/64 of the FP32 rate, so a pass that converts every point is FP64-bound
+// unless the conversion is done with integer operations.  Written from the
+// binary64 / binary32 formats: d2f_rn rounds to nearest, ties to even;
+// results below the smallest normal float flush to signed zero (f2d flushes
+// float subnormals the same way); overflow gives a signed infinity; a NaN
+// stays a (quiet) NaN.
+__device__ __forceinline__ float d2f_rn(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned int hi = (unsigned int)(u >> 32), lo = (unsigned int)u;
+  const unsigned int sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const unsigned int m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);   // top 23 mantissa bits
+  const unsigned int rest = lo & 0x1FFFFFFFu;                   // the 29 bits rounded off
+  const int ef = e - 1023 + 127;
+  unsigned int bits;
+  if (e == 0x7FF) {
+    bits = 0x7F800000u | ((m | rest) ? 0x400000u | m : 0u);
+  } else if (ef >= 0xFF) {
+    bits = 0x7F800000u;
+  } else if (ef <= 0) {
+    bits = 0u;
+  } else {
+    bits = ((unsigned int)ef << 23) | m;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) bits += 1u;   // may carry to inf
+  }
+  return __uint_as_float(bits | sign);
+}
+
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int sign = b & 0x80000000u;
+  const unsigned int e = (b >> 23) & 0xFFu;
+  const unsigned int m = b & 0x7FFFFFu;
+  unsigned int hi;
+  if (e == 0) return __longlong_as_double((long long)((unsigned long long)sign << 32));
+  if (e == 0xFF) hi = 0x7FF00000u | (m ? 0x80000u : 0u) | (m >> 3);
+  else hi = ((e + 896u) << 20) | (m >> 3);
+  return __longlong_as_double((long long)(((unsigned long long)(hi | sign) << 32) | (unsigned long long)(m << 29)));
+}
+
+// double -> double-float and back with one FP64 operation each.
+__device__ __forceinline__ df df_of(double d) {
+  const float h = d2f_rn(d);
+  return df(h, d2f_rn(d - f2d(h)));
+}
+__device__ __forceinline__ double dbl_of(df a) { return f2d(a.hi) + f2d(a.lo); }
+
 // Complex double-float (16 bytes, the size of a double2).
 struct __align__(16) dfc {
   df x, y;
@@ -138,7 +187,6 @@ __device__ __forceinline__ bool grid_reduce3(double a, double b, double c, doubl
                                              double* pc, unsigned int* counter, double* ra,
                                              double* rb, double* rc) {
   __shared__ double part[3][32];
-  __shared__ double tot[3];
   __shared__ bool am_last;
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
@@ -202,9 +250,6 @@ __device__ __forceinline__ bool grid_reduce3(double a, double b, double c, doubl
       sy += part[1][w];
       sz += part[2][w];
     }
-    tot[0] = sx;
-    tot[1] = sy;
-    tot[2] = sz;
     *ra = sx;
     *rb = sy;
     *rc = sz;

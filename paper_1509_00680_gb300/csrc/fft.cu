@@ -13,6 +13,7 @@
 // out of a shared-memory ping-pong pair with the twiddle table staged once.
 // The spectrum buffer holds only z < nz planes: [nz][Py][Hx] complex.
 #include <cstdio>
+#include <type_traits>
 
 #include "device_util.cuh"
 #include "gps_internal.h"
@@ -130,22 +131,31 @@ __host__ __device__ __forceinline__ int line_stride(int L) { return L + (L >> Pa
 
 // One Stockham stage over `nlines` lines of length L (line stride ls):
 // butterfly j gathers in[j + r L/R], twiddles by W_(Ns R)^(r k), k = j mod Ns,
-// and scatters to out[(j - k) R + k + r Ns].
-template <typename V, int DIR, int R>
+// and scatters to out[(j - k) R + k + r Ns].  Butterflies are dealt to the
+// threads round-robin over (line, j); a thread's next (line, j, k) follows
+// from the current one by constant steps (Ns divides L/R, so a wrap of j
+// leaves k unchanged), without a division per butterfly.  When L/R (FL) or
+// Ns (FS) is a multiple of the padding period, the padded index of element
+// r is the padded index of element 0 plus a constant times r.
+template <typename V, int DIR, int R, bool FL, bool FS>
 __device__ __forceinline__ void stage(const V* __restrict__ in, V* __restrict__ out, int L, int Ns,
                                       int ls, int nlines, const V* __restrict__ tw) {
+  constexpr int P = 1 << PadShift<V>::v;
   const int nb = L / R;
-  const int total = nb * nlines;
   const int tstep = L / (Ns * R);
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int line = idx / nb;
-    const int j = idx - line * nb;
+  const int snb = nb + nb / P, sns = Ns + Ns / P;
+  const int bd = blockDim.x;
+  const int dl = bd / nb, dj = bd - dl * nb, dk = dj % Ns;
+  int line = threadIdx.x / nb;
+  int j = threadIdx.x - line * nb;
+  int k = j % Ns;
+  while (line < nlines) {
     const V* src = in + line * ls;
     V* dst = out + line * ls;
     V x[R];
+    const int s0 = pidx<V>(j);
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = src[pidx<V>(j + r * nb)];
-    const int k = j % Ns;
+    for (int r = 0; r < R; ++r) x[r] = src[FL ? s0 + r * snb : pidx<V>(j + r * nb)];
     if (k != 0) {
       const int step = tstep * k;
 #pragma unroll
@@ -156,25 +166,45 @@ __device__ __forceinline__ void stage(const V* __restrict__ in, V* __restrict__ 
     }
     Dft<V, DIR, R>::run(x);
     const int base = (j - k) * R + k;
+    const int d0 = pidx<V>(base);
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[pidx<V>(base + r * Ns)] = x[r];
+    for (int r = 0; r < R; ++r) dst[FS ? d0 + r * sns : pidx<V>(base + r * Ns)] = x[r];
+    line += dl;
+    j += dj;
+    k += dk;
+    if (j >= nb) {
+      j -= nb;
+      ++line;
+    }
+    if (k >= Ns) k -= Ns;
   }
+}
+
+template <typename V, int DIR, int R>
+__device__ __forceinline__ void stage_any(const V* in, V* out, int L, int Ns, int ls, int nlines,
+                                          const V* tw) {
+  constexpr int P = 1 << PadShift<V>::v;
+  const bool fl = (L / R) % P == 0, fs = Ns % P == 0;
+  if (fl && fs) stage<V, DIR, R, true, true>(in, out, L, Ns, ls, nlines, tw);
+  else if (fl) stage<V, DIR, R, true, false>(in, out, L, Ns, ls, nlines, tw);
+  else if (fs) stage<V, DIR, R, false, true>(in, out, L, Ns, ls, nlines, tw);
+  else stage<V, DIR, R, false, false>(in, out, L, Ns, ls, nlines, tw);
 }
 
 // Full 1D transform of a batch of lines held in a; b is the ping-pong partner.
 // Returns the buffer holding the result.  Ends with a __syncthreads().
 template <typename V, int DIR>
-__device__ V* fft_lines(V* a, V* b, const FftSched& s, int ls, int nlines, const V* tw) {
+__device__ __forceinline__ V* fft_lines(V* a, V* b, const FftSched& s, int ls, int nlines, const V* tw) {
   V* in = a;
   V* out = b;
   for (int st = 0; st < s.nst; ++st) {
     const int R = s.radix[st], Ns = s.ns[st];
     switch (R) {
-      case 2: stage<V, DIR, 2>(in, out, s.L, Ns, ls, nlines, tw); break;
-      case 3: stage<V, DIR, 3>(in, out, s.L, Ns, ls, nlines, tw); break;
-      case 4: stage<V, DIR, 4>(in, out, s.L, Ns, ls, nlines, tw); break;
-      case 5: stage<V, DIR, 5>(in, out, s.L, Ns, ls, nlines, tw); break;
-      default: stage<V, DIR, 8>(in, out, s.L, Ns, ls, nlines, tw); break;
+      case 2: stage_any<V, DIR, 2>(in, out, s.L, Ns, ls, nlines, tw); break;
+      case 3: stage_any<V, DIR, 3>(in, out, s.L, Ns, ls, nlines, tw); break;
+      case 4: stage_any<V, DIR, 4>(in, out, s.L, Ns, ls, nlines, tw); break;
+      case 5: stage_any<V, DIR, 5>(in, out, s.L, Ns, ls, nlines, tw); break;
+      default: stage_any<V, DIR, 8>(in, out, s.L, Ns, ls, nlines, tw); break;
     }
     __syncthreads();
     V* t = in;
@@ -191,6 +221,11 @@ __device__ __forceinline__ size_t row_offset(const PassGeom& g, int row) {
 
 constexpr int kThreads = 256;
 
+// Resident blocks per SM asked of the register allocator: FP32 passes keep
+// <= 64 registers a thread, FP64 and df64 passes <= 128.
+template <typename V> struct MinBlocks { static constexpr int v = 2; };
+template <> struct MinBlocks<float2> { static constexpr int v = 4; };
+
 // Slot served by this block for a spectrum pass of precision V, or -1.
 template <typename V>
 __device__ __forceinline__ int pass_slot(const Batch& b) {
@@ -198,6 +233,89 @@ __device__ __forceinline__ int pass_slot(const Batch& b) {
   if (s >= 0 && b.st && b.prec >= 0 && b.st[s].spec != SpecOf<V>::v) s = -1;
   if (s >= 0) mark_acted(b);
   return s;
+}
+
+// Round-robin walk of the block's threads over (l, j) in [0, nl) x [0, J),
+// with one division at the start.
+struct LineIter {
+  int l, j, dl, dj, J;
+  __device__ explicit LineIter(int J_) : J(J_) {
+    l = threadIdx.x / J;
+    j = threadIdx.x - l * J;
+    dl = blockDim.x / J;
+    dj = blockDim.x - dl * J;
+  }
+  __device__ void next() {
+    l += dl;
+    j += dj;
+    if (j >= J) {
+      j -= J;
+      ++l;
+    }
+  }
+};
+
+constexpr int kMaxLinesX = 64;
+
+// Loads issued before their shared-memory stores, per thread and batch: the
+// stores go through generic pointers that the compiler must assume may alias
+// the loads, so without batching each thread would keep a single HBM load in
+// flight.
+template <typename V> struct Batch_ { static constexpr int v = sizeof(V) == 8 ? 8 : 4; };
+
+// line[pidx(y)] = y < nload ? col[y * stride] : 0 for y = y0, y0 + ystep, ... < L.
+template <typename V>
+__device__ __forceinline__ void load_column(V* line, const V* __restrict__ col, size_t stride, int y0,
+                                            int ystep, int L, int nload) {
+  constexpr int U = Batch_<V>::v;
+  for (int yb = y0; yb < L; yb += U * ystep) {
+    V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int y = yb + u * ystep;
+      v[u] = y < nload ? col[(size_t)y * stride] : czero<V>();
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int y = yb + u * ystep;
+      if (y < L) line[pidx<V>(y)] = v[u];
+    }
+  }
+}
+
+// Spectrum offsets of the two rows of each pair handled by the block
+// (row_offset needs a division per row).
+template <typename V>
+__device__ __forceinline__ void pair_offsets(const PassGeom& g, int p0, int nl, size_t* off) {
+  for (int t = threadIdx.x; t < 2 * nl; t += blockDim.x) {
+    const int row = 2 * p0 + t;
+    off[t] = row < g.nrows ? row_offset(g, row) : 0;
+  }
+}
+
+// Input value of the x pass: in * scale, rounded to the spectrum's real type.
+// The FP32 spectrum multiplies in FP32 unless the FP64 sum of the products is
+// wanted; conversions run on the integer pipe.
+template <typename V>
+__device__ __forceinline__ typename Real<V>::T load_scaled(const double* in, const double* scale,
+                                                           size_t o, bool red, double& sum) {
+  if constexpr (std::is_same<V, float2>::value) {
+    if (red) {
+      double v = in[o];
+      if (scale) v *= scale[o];
+      sum += v;
+      return d2f_rn(v);
+    }
+    float v = d2f_rn(in[o]);
+    if (scale) v *= d2f_rn(scale[o]);
+    return v;
+  } else {
+    double v = in[o];
+    if (scale) v *= scale[o];
+    if (red) sum += v;
+    if constexpr (std::is_same<V, dfc>::value) return df_of(v);
+    else return v;
+  }
 }
 
 template <typename V>
@@ -210,6 +328,7 @@ __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, cons
   const double* __restrict__ scale = a.in_scale ? a.in_scale + slot * b.vstride : nullptr;
   V* __restrict__ W = reinterpret_cast<V*>(a.W) + slot * a.wstride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ size_t woff[2 * kMaxLinesX];
   V* tw = reinterpret_cast<V*>(smem_raw);
   const int L = s.L, ls = line_stride<V>(L);
   V* b0 = tw + L;
@@ -218,35 +337,50 @@ __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, cons
   const int npairs = (g.nrows + 1) >> 1;
   const int p0 = blockIdx.x * g.lines_x;
   const int nl = min(g.lines_x, npairs - p0);
+  pair_offsets<V>(g, p0, nl, woff);
+  const bool red = a.red_mu && b.st;
   double sum = 0.0;
-  for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-    const int l = idx / L, j = idx - l * L;
-    const int ra = 2 * (p0 + l);
-    double va = 0.0, vb = 0.0;
-    if (j < g.nx) {
-      const size_t oa = (size_t)ra * g.nx + j;
-      va = in[oa];
-      if (scale) va *= scale[oa];
-      if (ra + 1 < g.nrows) {
-        vb = in[oa + g.nx];
-        if (scale) vb *= scale[oa + g.nx];
+  {
+    constexpr int U = 4;
+    LineIter it(L);
+    while (it.l < nl) {
+      T va[U], vb[U];
+      int dst[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        va[u] = T(0);
+        vb[u] = T(0);
+        dst[u] = -1;
+        if (it.l < nl) {
+          const int l = it.l, j = it.j;
+          const int ra = 2 * (p0 + l);
+          if (j < g.nx) {
+            const size_t oa = (size_t)ra * g.nx + j;
+            va[u] = load_scaled<V>(in, scale, oa, red, sum);
+            if (ra + 1 < g.nrows) vb[u] = load_scaled<V>(in, scale, oa + g.nx, red, sum);
+          }
+          dst[u] = l * ls + pidx<V>(j);
+          it.next();
+        }
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (dst[u] >= 0) b0[dst[u]] = mk<V>(va[u], vb[u]);
     }
-    sum += va + vb;
-    b0[l * ls + pidx<V>(j)] = mk<V>((T)va, (T)vb);
   }
   __syncthreads();
   const V* res = fft_lines<V, -1>(b0, b1, s, ls, nl, tw);
-  for (int idx = threadIdx.x; idx < nl * g.Hx; idx += blockDim.x) {
-    const int l = idx / g.Hx, k = idx - l * g.Hx;
-    const V zk = res[l * ls + pidx<V>(k)];
-    const V zm = res[l * ls + pidx<V>(k == 0 ? 0 : L - k)];
-    const int ra = 2 * (p0 + l);
+  const T half = T(0.5);
+  for (LineIter it(g.Hx); it.l < nl; it.next()) {
+    const int l = it.l, k = it.j;
+    const V* line = res + l * ls;
+    const V zk = line[pidx<V>(k)];
+    const V zm = line[pidx<V>(k == 0 ? 0 : L - k)];
     // A_k = (Z_k + conj Z_(L-k))/2 ; B_k = -i (Z_k - conj Z_(L-k))/2
-    W[row_offset(g, ra) + k] = mk<V>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
-    if (ra + 1 < g.nrows) W[row_offset(g, ra + 1) + k] = mk<V>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
+    W[woff[2 * l] + k] = mk<V>(half * (zk.x + zm.x), half * (zk.y - zm.y));
+    if (2 * (p0 + l) + 1 < g.nrows) W[woff[2 * l + 1] + k] = mk<V>(half * (zk.y + zm.y), half * (zm.x - zk.x));
   }
-  if (a.red_mu && b.st)
+  if (red)
     grid_reduce(sum, b.partials + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_MU], &b.st[slot].mu_sum);
 }
 
@@ -267,18 +401,17 @@ __global__ void __launch_bounds__(kThreads) k_y(PassGeom g, FftSched s, const V*
   const int z = blockIdx.y;
   const size_t plane = (size_t)z * g.Py * g.Hx;
   const int nload = DIR < 0 ? g.ny : L;   // forward: rows y >= ny are the zero padding
-  for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-    const int y = idx / nl, c = idx - y * nl;
-    V v = czero<V>();
-    if (y < nload) v = W[plane + (size_t)y * g.Hx + kx0 + c];
-    b0[c * ls + pidx<V>(y)] = v;
-  }
+  // thread -> (column c, first row y0); rows advance by ystep
+  const int c = threadIdx.x % tile, y0 = threadIdx.x / tile, ystep = blockDim.x / tile;
+  const bool act = c < nl && y0 < ystep;
+  V* col = W + plane + kx0 + c;
+  if (act) load_column<V>(b0 + c * ls, col, g.Hx, y0, ystep, L, nload);
   __syncthreads();
   const V* res = fft_lines<V, DIR>(b0, b1, s, ls, nl, tw);
   const int nstore = DIR < 0 ? L : g.ny;  // inverse: crop to y < ny
-  for (int idx = threadIdx.x; idx < nl * nstore; idx += blockDim.x) {
-    const int y = idx / nl, c = idx - y * nl;
-    W[plane + (size_t)y * g.Hx + kx0 + c] = res[c * ls + pidx<V>(y)];
+  if (act) {
+    const V* line = res + c * ls;
+    for (int y = y0; y < nstore; y += ystep) col[(size_t)y * g.Hx] = line[pidx<V>(y)];
   }
 }
 
@@ -302,32 +435,88 @@ __global__ void __launch_bounds__(kThreads) k_z(PassGeom g, FftSched s, const V*
   const int ky = blockIdx.y;
   const size_t colbase = (size_t)ky * g.Hx + kx0;
   const size_t zstride = (size_t)g.Py * g.Hx;
-  for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-    const int z = idx / nl, c = idx - z * nl;
-    V v = czero<V>();
-    if (z < g.nz) v = W[(size_t)z * zstride + colbase + c];
-    b0[c * ls + pidx<V>(z)] = v;
-  }
+  // thread -> (column c, first plane z0); planes advance by zstep
+  const int c = threadIdx.x % tile, z0 = threadIdx.x / tile, zstep = blockDim.x / tile;
+  const bool act = c < nl && z0 < zstep;
+  V* col = W + colbase + c;
+  if (act) load_column<V>(b0 + c * ls, col, zstride, z0, zstep, L, g.nz);
   __syncthreads();
   V* res = fft_lines<V, -1>(b0, b1, s, ls, nl, tw);
   V* other = (res == b0) ? b1 : b0;
   const int kyp = min(ky, g.Py - ky);
   const int hy = g.Py / 2 + 1;
-  for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-    const int kz = idx / nl, c = idx - kz * nl;
+  if (act) {
     const int kx = kx0 + c;
-    const int kzp = min(kz, L - kz);
-    double t = a.table[((size_t)kzp * hy + kyp) * g.Hx + kx];
-    if (use_k0 && kx == 0 && ky == 0 && kz == 0) t = k0;
-    const int pk = c * ls + pidx<V>(kz);
-    res[pk] = cscale(res[pk], (T)t);
+    const size_t t0 = (size_t)kyp * g.Hx + kx;   // + kzp * hy * Hx
+    const size_t tz = (size_t)hy * g.Hx;
+    V* line = res + c * ls;
+    const bool at0 = use_k0 && kx == 0 && ky == 0;
+    constexpr int U = 8;
+    for (int kb = z0; kb < L; kb += U * zstep) {
+      T t[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int kz = min(kb + u * zstep, L - 1);
+        const int kzp = min(kz, L - kz);
+        const size_t ti = t0 + kzp * tz;
+        if constexpr (std::is_same<V, float2>::value) {
+          t[u] = a.table32 ? a.table32[ti] : d2f_rn(a.table[ti]);
+        } else if constexpr (std::is_same<V, dfc>::value) {
+          if (a.tabledf) {
+            const float2 h = a.tabledf[ti];
+            t[u] = df(h.x, h.y);
+          } else {
+            t[u] = df_of(a.table[ti]);
+          }
+        } else {
+          t[u] = a.table[ti];
+        }
+      }
+      if (at0 && kb == 0) {
+        if constexpr (std::is_same<V, float2>::value) t[0] = d2f_rn(k0);
+        else if constexpr (std::is_same<V, dfc>::value) t[0] = df_of(k0);
+        else t[0] = k0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int kz = kb + u * zstep;
+        if (kz < L) {
+          const int pk = pidx<V>(kz);
+          line[pk] = cscale(line[pk], t[u]);
+        }
+      }
+    }
   }
   __syncthreads();
   const V* fin = fft_lines<V, +1>(res, other, s, ls, nl, tw);
-  for (int idx = threadIdx.x; idx < nl * g.nz; idx += blockDim.x) {
-    const int z = idx / nl, c = idx - z * nl;
-    W[(size_t)z * zstride + colbase + c] = fin[c * ls + pidx<V>(z)];
+  if (act) {
+    const V* line = fin + c * ls;
+    for (int z = z0; z < g.nz; z += zstep) col[(size_t)z * zstride] = line[pidx<V>(z)];
   }
+}
+
+// Real output value of the x inverse pass as a double (integer-pipe
+// conversions; the FP32 spectrum scales in FP32).
+template <typename V>
+__device__ __forceinline__ double out_value(typename Real<V>::T z, const double* scale, size_t o) {
+  if constexpr (std::is_same<V, float2>::value) {
+    float v = z;
+    if (scale) v *= d2f_rn(scale[o]);
+    return f2d(v);
+  } else {
+    double v;
+    if constexpr (std::is_same<V, dfc>::value) v = dbl_of(z);
+    else v = z;
+    if (scale) v *= scale[o];
+    return v;
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ double unscaled(typename Real<V>::T z) {
+  if constexpr (std::is_same<V, float2>::value) return f2d(z);
+  else if constexpr (std::is_same<V, dfc>::value) return dbl_of(z);
+  else return z;
 }
 
 template <typename V>
@@ -341,6 +530,7 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
   const double* __restrict__ out_scale = a.out_scale ? a.out_scale + slot * b.vstride : nullptr;
   const double* __restrict__ dot_with = a.dot_with ? a.dot_with + slot * b.vstride : nullptr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ size_t woff[2 * kMaxLinesX];
   V* tw = reinterpret_cast<V*>(smem_raw);
   const int L = s.L, ls = line_stride<V>(L);
   V* b0 = tw + L;
@@ -349,47 +539,66 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
   const int npairs = (g.nrows + 1) >> 1;
   const int p0 = blockIdx.x * g.lines_x;
   const int nl = min(g.lines_x, npairs - p0);
-  for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-    const int l = idx / L, k = idx - l * L;
-    const int ra = 2 * (p0 + l);
-    const bool hasb = ra + 1 < g.nrows;
-    V A, B;
-    if (k < g.Hx) {
-      A = W[row_offset(g, ra) + k];
-      B = hasb ? W[row_offset(g, ra + 1) + k] : czero<V>();
-      if (k == 0 || 2 * k == L) { A.y = T(0); B.y = T(0); }   // DC and Nyquist are real
-    } else {
-      const int m = L - k;
-      A = cconj(W[row_offset(g, ra) + m]);
-      B = hasb ? cconj(W[row_offset(g, ra + 1) + m]) : czero<V>();
+  pair_offsets<V>(g, p0, nl, woff);
+  __syncthreads();
+  {
+    constexpr int U = Batch_<V>::v / 2;
+    LineIter it(L);
+    while (it.l < nl) {
+      V A[U], B[U];
+      int dst[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        dst[u] = -1;
+        A[u] = czero<V>();
+        B[u] = czero<V>();
+        if (it.l < nl) {
+          const int l = it.l, k = it.j;
+          const bool hasb = 2 * (p0 + l) + 1 < g.nrows;
+          const V* wa = W + woff[2 * l];
+          const V* wb = W + woff[2 * l + 1];
+          if (k < g.Hx) {
+            A[u] = wa[k];
+            if (hasb) B[u] = wb[k];
+          } else {
+            const int m = L - k;
+            A[u] = cconj(wa[m]);
+            if (hasb) B[u] = cconj(wb[m]);
+          }
+          if (k == 0 || 2 * k == L) { A[u].y = T(0); B[u].y = T(0); }   // DC and Nyquist are real
+          dst[u] = l * ls + pidx<V>(k);
+          it.next();
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (dst[u] >= 0) b0[dst[u]] = mk<V>(A[u].x - B[u].y, A[u].y + B[u].x);   // Z = A + i B
     }
-    b0[l * ls + pidx<V>(k)] = mk<V>(A.x - B.y, A.y + B.x);   // Z = A + i B
   }
   __syncthreads();
   const V* res = fft_lines<V, +1>(b0, b1, s, ls, nl, tw);
+  const bool want_wsum = a.red_wsum && b.st && b.st[slot].gauge;
   double dot = 0.0, wsum = 0.0;
-  for (int idx = threadIdx.x; idx < nl * g.nx; idx += blockDim.x) {
-    const int l = idx / g.nx, j = idx - l * g.nx;
+  for (LineIter it(g.nx); it.l < nl; it.next()) {
+    const int l = it.l, j = it.j;
     const int ra = 2 * (p0 + l);
     const V zz = res[l * ls + pidx<V>(j)];
     const size_t oa = (size_t)ra * g.nx + j;
-    wsum += (double)zz.x;
-    double va = (double)zz.x;
-    if (out_scale) va *= out_scale[oa];
+    const double va = out_value<V>(zz.x, out_scale, oa);
     out[oa] = va;
     if (dot_with) dot += va * dot_with[oa];
+    if (want_wsum) wsum += unscaled<V>(zz.x);
     if (ra + 1 < g.nrows) {
       const size_t ob = oa + g.nx;
-      wsum += (double)zz.y;
-      double vb = (double)zz.y;
-      if (out_scale) vb *= out_scale[ob];
+      const double vb = out_value<V>(zz.y, out_scale, ob);
       out[ob] = vb;
       if (dot_with) dot += vb * dot_with[ob];
+      if (want_wsum) wsum += unscaled<V>(zz.y);
     }
   }
   if (dot_with && b.st)
     grid_reduce(dot, b.partials + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_VR], &b.st[slot].vr);
-  if (a.red_wsum && b.st && b.st[slot].gauge)
+  if (want_wsum)
     grid_reduce(wsum, b.partials2 + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_WSUM],
                 &b.st[slot].wsum);
 }

@@ -120,6 +120,8 @@ struct PipeArgs {
   const double* out_scale;  // optional factor (s or sqrt(eps))
   const double* dot_with;   // optional: reduce (out, dot_with) into st.vr
   const double* table;      // normalized octant Green's / Laplacian table
+  const float* table32;     // optional: the table rounded to float (FP32 spectrum)
+  const float2* tabledf;    // optional: the table as double-float (hi, lo) (df64 spectrum)
   void* W;                  // spectrum base (slot 0)
   size_t wstride;           // complex elements between slots
   int slot_k0;              // use st[slot].k0 for k = 0 when st[slot].use_k0

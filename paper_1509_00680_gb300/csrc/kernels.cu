@@ -34,7 +34,10 @@ unsigned long long launch_count() { return g_launches.load(std::memory_order_rel
 
 int grid_blocks(size_t n, int threads) {
   size_t b = (n + threads - 1) / threads;
-  const size_t cap = 152 * 8;   // SMs x resident blocks of 256 threads
+  // 4 blocks of 256 threads on each of the 152 SMs: every block is resident
+  // at once for any kernel of up to 64 registers, so no second partial wave
+  // of blocks runs after the first (each thread loops over its elements).
+  const size_t cap = 152 * 4;
   if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (int)b;
@@ -268,19 +271,20 @@ __global__ void k_init(Batch b, Fields f, size_t n) {
 // the directions (beta = 0) instead of stopping.
 __global__ void k_update_p(Batch b, Fields f, size_t n, double inv_n, int periodic) {
   SLOT_PROLOGUE(b)
-  const double* v = f.v + off;
-  const double* r = f.r + off;
-  const double* qlam = f.qlam + off;
-  const double* sqe = f.sq + off;
-  const double* s = f.s + off;
-  double* p = f.p + off;
-  double* Ap = f.Ap + off;
+  const double* __restrict__ v = f.v + off;
+  const double* __restrict__ r = f.r + off;
+  const double* __restrict__ qlam = f.qlam + off;
+  const double* __restrict__ sqe = f.sq + off;
+  const double* __restrict__ s = f.s + off;
+  double* __restrict__ p = f.p + off;
+  double* __restrict__ Ap = f.Ap + off;
   const bool project = S.gauge != 0;
   const double c = project ? S.wsum * inv_n : 0.0;
   const double vr = project ? S.vr - c * S.mu_sum : S.vr;
   const double beta = (S.iter == 0 || S.restart) ? 0.0 : vr / S.vr_prev;
   const double mu4pi = periodic ? kFourPi * S.mu_sum * inv_n : 0.0;
   double acc = 0.0, ap_acc = 0.0, p_acc = 0.0;
+#pragma unroll 2
   GRID_STRIDE(i, n) {
     const double vi = project ? v[i] - c * s[i] : v[i];
     double av = -qlam[i] * vi - kFourPi * r[i];
@@ -330,18 +334,18 @@ __global__ void k_update_p(Batch b, Fields f, size_t n, double inv_n, int period
 __global__ void k_update_r(Batch b, Fields f, size_t n) {
   SLOT_PROLOGUE(b)
   const bool nl = S.kind == GPS_NLPB;
-  double* x = (nl ? f.dphi : f.phi) + off;
-  double* r = f.r + off;
-  const double* p = f.p + off;
-  const double* Ap = f.Ap + off;
+  double* __restrict__ x = (nl ? f.dphi : f.phi) + off;
+  double* __restrict__ r = f.r + off;
+  const double* __restrict__ p = f.p + off;
+  double* __restrict__ Ap = f.Ap + off;
   const double alpha = S.alpha;
   const double m = S.gauge ? S.ap_mean : 0.0;
-  double* Apw = f.Ap + off;
   double acc = 0.0;
+#pragma unroll 2
   GRID_STRIDE(i, n) {
     x[i] += alpha * p[i];
     const double api = Ap[i] - m;
-    if (m != 0.0) Apw[i] = api;   // keep the projected A p for the recurrence
+    if (m != 0.0) Ap[i] = api;   // keep the projected A p for the recurrence
     const double ri = r[i] - alpha * api;
     r[i] = ri;
     acc += ri * ri;
@@ -685,6 +689,22 @@ void launch_fp_residual(const Batch& b, const Fields& f, size_t n, int periodic,
                         cudaStream_t st) {
   count_launch();
   k_fp_residual<<<VEC_GRID(n, nslots)>>>(b, f, n, periodic);
+}
+
+// Float and double-float copies of a Green's table, made once per shape.
+__global__ void k_table_split(const double* __restrict__ t, float* __restrict__ t32,
+                              float2* __restrict__ tdf, size_t n) {
+  GRID_STRIDE(i, n) {
+    const double v = t[i];
+    const float hi = (float)v;
+    t32[i] = hi;
+    tdf[i] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+
+void launch_table_split(const double* t, float* t32, float2* tdf, size_t n, cudaStream_t st) {
+  count_launch();
+  k_table_split<<<grid_blocks(n, kT), kT, 0, st>>>(t, t32, tdf, n);
 }
 
 void launch_ionic_charge(const double* phi, const double* eps, double* out, size_t n,

@@ -41,6 +41,7 @@ void launch_nl_step(const Batch& b, const Fields& f, size_t n, int commit, int n
 void launch_fp_source(const Batch& b, const Fields& f, size_t n, int nslots, cudaStream_t st);
 void launch_fp_residual(const Batch& b, const Fields& f, size_t n, int periodic, int nslots,
                         cudaStream_t st);
+void launch_table_split(const double* t, float* t32, float2* tdf, size_t n, cudaStream_t st);
 void launch_ionic_charge(const double* phi, const double* eps, double* out, size_t n,
                          const IonParams& ip, cudaStream_t st);
 void launch_table_periodic(double* kern, double* lap, int Hx, int hy, int hz, double dkx, double dky,
