@@ -111,6 +111,12 @@ def peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel on this workload, from the ncu capture summarized in
+# profiles/k_z_gpe_periodic_128.md (to be retaken whenever the kernel changes).
+NCU_TRAFFIC = {"z": 19354112}
+
+
 def pass_geometry(grid):
     free = grid.bc == 0
     fz = grid.bc != 1
@@ -222,7 +228,7 @@ def run_ours(args, ws, rank, local):
     fl = kernel_flops(dom, P)
     ach = fl / (avg_ms / 1e3) / 1e12
     roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(dom),
             "avg_launch_ms": avg_ms, "launches_timed": n_l,
             "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)",
             "flops_model": "5 L log2 L per complex FFT of length L (+2 per point for the table)",

@@ -15,119 +15,9 @@
 #include <cstdio>
 #include <type_traits>
 
-#include "device_util.cuh"
-#include "gps_internal.h"
+#include "fft_common.cuh"
 
 namespace gps {
-
-// Radix-R butterflies, DIR = -1 forward (e^{-2 pi i/R}), +1 inverse.
-template <typename V, int DIR>
-__device__ __forceinline__ V rot_i(V a) {  // a * (DIR * i)
-  return DIR < 0 ? mk<V>(a.y, -a.x) : mk<V>(-a.y, a.x);
-}
-
-template <typename V, int DIR, int R> struct Dft;
-
-template <typename V, int DIR> struct Dft<V, DIR, 2> {
-  __device__ __forceinline__ static void run(V* x) {
-    V a = x[0], b = x[1];
-    x[0] = cadd(a, b);
-    x[1] = csub(a, b);
-  }
-};
-
-template <typename V, int DIR> struct Dft<V, DIR, 4> {
-  __device__ __forceinline__ static void run(V* x) {
-    V a0 = cadd(x[0], x[2]), a1 = csub(x[0], x[2]);
-    V a2 = cadd(x[1], x[3]), a3 = rot_i<V, DIR>(csub(x[1], x[3]));
-    x[0] = cadd(a0, a2);
-    x[2] = csub(a0, a2);
-    x[1] = cadd(a1, a3);
-    x[3] = csub(a1, a3);
-  }
-};
-
-template <typename V, int DIR> struct Dft<V, DIR, 8> {
-  __device__ __forceinline__ static void run(V* x) {
-    using T = typename Real<V>::T;
-    const T c = (T)0.70710678118654752440;  // sqrt(1/2)
-    V e[4] = {x[0], x[2], x[4], x[6]};
-    V o[4] = {x[1], x[3], x[5], x[7]};
-    Dft<V, DIR, 4>::run(e);
-    Dft<V, DIR, 4>::run(o);
-    // o_k *= e^{DIR 2 pi i k / 8}
-    if (DIR < 0) {
-      o[1] = mk<V>(c * (o[1].x + o[1].y), c * (o[1].y - o[1].x));
-      o[2] = mk<V>(o[2].y, -o[2].x);
-      o[3] = mk<V>(c * (o[3].y - o[3].x), -c * (o[3].x + o[3].y));
-    } else {
-      o[1] = mk<V>(c * (o[1].x - o[1].y), c * (o[1].x + o[1].y));
-      o[2] = mk<V>(-o[2].y, o[2].x);
-      o[3] = mk<V>(-c * (o[3].x + o[3].y), c * (o[3].x - o[3].y));
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      x[k] = cadd(e[k], o[k]);
-      x[k + 4] = csub(e[k], o[k]);
-    }
-  }
-};
-
-template <typename V, int DIR> struct Dft<V, DIR, 3> {
-  __device__ __forceinline__ static void run(V* x) {
-    using T = typename Real<V>::T;
-    const T s3 = (T)0.86602540378443864676;  // sqrt(3)/2
-    V t1 = cadd(x[1], x[2]);
-    V t2 = mk<V>(x[0].x - (T)0.5 * t1.x, x[0].y - (T)0.5 * t1.y);
-    V d = csub(x[1], x[2]);
-    V u = mk<V>((T)DIR * s3 * d.x, (T)DIR * s3 * d.y);   // u = DIR s3 (x1 - x2)
-    V iu = mk<V>(-u.y, u.x);
-    x[0] = cadd(x[0], t1);
-    x[1] = cadd(t2, iu);
-    x[2] = csub(t2, iu);
-  }
-};
-
-template <typename V, int DIR> struct Dft<V, DIR, 5> {
-  __device__ __forceinline__ static void run(V* x) {
-    using T = typename Real<V>::T;
-    const T c1 = (T)0.30901699437494742410;   // cos(2 pi/5) = (sqrt5 - 1)/4
-    const T c2 = (T)-0.80901699437494742410;  // cos(4 pi/5) = -(sqrt5 + 1)/4
-    const T s1 = (T)0.95105651629515357212;   // sin(2 pi/5)
-    const T s2 = (T)0.58778525229247312917;   // sin(4 pi/5)
-    V a1 = cadd(x[1], x[4]), b1 = csub(x[1], x[4]);
-    V a2 = cadd(x[2], x[3]), b2 = csub(x[2], x[3]);
-    V p1 = mk<V>(x[0].x + c1 * a1.x + c2 * a2.x, x[0].y + c1 * a1.y + c2 * a2.y);
-    V p2 = mk<V>(x[0].x + c2 * a1.x + c1 * a2.x, x[0].y + c2 * a1.y + c1 * a2.y);
-    V q1 = mk<V>((T)DIR * (s1 * b1.x + s2 * b2.x), (T)DIR * (s1 * b1.y + s2 * b2.y));
-    V q2 = mk<V>((T)DIR * (s2 * b1.x - s1 * b2.x), (T)DIR * (s2 * b1.y - s1 * b2.y));
-    V iq1 = mk<V>(-q1.y, q1.x), iq2 = mk<V>(-q2.y, q2.x);
-    x[0] = cadd(x[0], cadd(a1, a2));
-    x[1] = cadd(p1, iq1);
-    x[4] = csub(p1, iq1);
-    x[2] = cadd(p2, iq2);
-    x[3] = csub(p2, iq2);
-  }
-};
-
-// Shared-memory layout of a line: one pad element after every 128 bytes
-// (8 complex doubles, 16 complex floats), so that the stride-R scatters of
-// the early Stockham stages spread over all banks.
-template <typename V> struct PadShift;
-template <> struct PadShift<double2> { static constexpr int v = 3; };
-template <> struct PadShift<float2> { static constexpr int v = 4; };
-template <> struct PadShift<dfc> { static constexpr int v = 3; };
-
-template <typename V> struct SpecOf;
-template <> struct SpecOf<double2> { static constexpr int v = SPEC_FP64; };
-template <> struct SpecOf<float2> { static constexpr int v = SPEC_FP32; };
-template <> struct SpecOf<dfc> { static constexpr int v = SPEC_DF64; };
-
-template <typename V>
-__device__ __forceinline__ int pidx(int i) { return i + (i >> PadShift<V>::v); }
-
-template <typename V>
-__host__ __device__ __forceinline__ int line_stride(int L) { return L + (L >> PadShift<V>::v) + 1; }
 
 // One Stockham stage over `nlines` lines of length L (line stride ls):
 // butterfly j gathers in[j + r L/R], twiddles by W_(Ns R)^(r k), k = j mod Ns,
@@ -212,27 +102,6 @@ __device__ __forceinline__ V* fft_lines(V* a, V* b, const FftSched& s, int ls, i
     out = t;
   }
   return in;
-}
-
-__device__ __forceinline__ size_t row_offset(const PassGeom& g, int row) {
-  const int y = row % g.ny, z = row / g.ny;
-  return ((size_t)z * g.Py + y) * g.Hx;
-}
-
-constexpr int kThreads = 256;
-
-// Resident blocks per SM asked of the register allocator: FP32 passes keep
-// <= 64 registers a thread, FP64 and df64 passes <= 128.
-template <typename V> struct MinBlocks { static constexpr int v = 2; };
-template <> struct MinBlocks<float2> { static constexpr int v = 4; };
-
-// Slot served by this block for a spectrum pass of precision V, or -1.
-template <typename V>
-__device__ __forceinline__ int pass_slot(const Batch& b) {
-  int s = batch_slot(b);
-  if (s >= 0 && b.st && b.prec >= 0 && b.st[s].spec != SpecOf<V>::v) s = -1;
-  if (s >= 0) mark_acted(b);
-  return s;
 }
 
 // Round-robin walk of the block's threads over (l, j) in [0, nl) x [0, J),
@@ -633,6 +502,7 @@ void launch_x_fwd(const PassGeom& g, const FftSched& s, const V* tw, const Batch
 template <typename V>
 void launch_y(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
               const PipeArgs& a, bool inverse, int nslots, cudaStream_t st) {
+  if (launch_col_pass<V>(inverse ? 1 : 0, s.L, g, tw, b, a, nslots, st)) return;
   dim3 grid((g.Hx + g.tile_y - 1) / g.tile_y, g.nz, nslots);
   const size_t sm = x_lines_smem_bytes(s.L, g.tile_y, sizeof(V));
   count_launch();
@@ -648,6 +518,7 @@ void launch_y(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
 template <typename V>
 void launch_z(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
               const PipeArgs& a, int nslots, cudaStream_t st) {
+  if (launch_col_pass<V>(2, s.L, g, tw, b, a, nslots, st)) return;
   dim3 grid((g.Hx + g.tile_z - 1) / g.tile_z, g.Py, nslots);
   const size_t sm = x_lines_smem_bytes(s.L, g.tile_z, sizeof(V));
   set_smem(k_z<V>, sm);

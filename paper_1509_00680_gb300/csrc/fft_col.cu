@@ -1,0 +1,258 @@
+// Register-resident column transforms of the y and z spectrum passes for
+// power-of-two lengths L = 64 .. 1024 (the padded lengths of the common
+// grids).  Other lengths use the shared-memory Stockham kernels of fft.cu.
+//
+// A CTA of 256 threads transforms TC = 256 / (L/E) adjacent columns of the
+// spectrum; each thread holds E (8 or 16) elements of one column in
+// registers.  The
+// first Stockham stage reads its elements straight from HBM and the last one
+// writes straight back; between stages the elements go through one padded
+// shared-memory line per column.  All index arithmetic is compile-time.
+//
+// The z pass (Eq. PCGdef: forward FFT, multiply by the Green's-function
+// table, inverse FFT, crop) runs the inverse with the forward's radices in
+// reverse order: the forward's last stage leaves in each thread the elements
+// b + r L/R that the inverse's first stage reads, so the table multiply and
+// the hand-over between the two transforms happen in registers.
+#include <cstdio>
+
+#include "fft_common.cuh"
+
+
+namespace gps {
+namespace {
+
+// Radix plan: radix-8 stages, then one stage of radix L / 8^k when L is not a
+// power of 8.  rev = true gives the stages in reverse order.
+template <int L> struct ColPlan {
+  static_assert(L == 64 || L == 128 || L == 256 || L == 512 || L == 1024, "unsupported length");
+  static constexpr int nst = L == 64 ? 2 : L == 1024 ? 4 : 3;
+  static constexpr int last = L == 128 ? 2 : L == 256 ? 4 : L == 1024 ? 2 : 8;
+  __host__ __device__ static constexpr int radix(int s, bool rev) {
+    return (rev ? nst - 1 - s : s) == nst - 1 ? last : 8;
+  }
+  __host__ __device__ static constexpr int ns(int s, bool rev) {
+    int p = 1;
+    for (int i = 0; i < s; ++i) p *= radix(i, rev);
+    return p;
+  }
+};
+
+// Butterflies of one stage (radix R, Ns = NS) on the thread's E elements:
+// butterfly q is b = t + q L/E with inputs x[q R + r] = in[b + r L/R].
+template <typename V, int L, int E, int DIR, int R, int NS>
+__device__ __forceinline__ void col_butterflies(V (&x)[E], int t, const V* tw) {
+  constexpr int TPC = L / E, Q = E / R;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    if constexpr (NS > 1) {
+      constexpr int TS = L / (NS * R);
+      const int k = (t + q * TPC) & (NS - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const V w = tw[r * k * TS];
+        x[q * R + r] = DIR < 0 ? cmul(x[q * R + r], w) : cmulc(x[q * R + r], w);
+      }
+    }
+    Dft<V, DIR, R>::run(x + q * R);
+  }
+}
+
+// Scatter of a stage's outputs to out[(b - k) R + k + r Ns] in the column's
+// shared line, then gather of the next stage's inputs in[b + r L/R2].
+template <typename V, int L, int E, int R, int NS, int R2>
+__device__ __forceinline__ void col_exchange(V (&x)[E], int t, V* line) {
+  constexpr int TPC = L / E;
+#pragma unroll
+  for (int q = 0; q < E / R; ++q) {
+    const int b = t + q * TPC;
+    const int k = b & (NS - 1);
+    const int base = (b - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) line[pidx<V>(base + r * NS)] = x[q * R + r];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < E / R2; ++q) {
+    const int b = t + q * TPC;
+#pragma unroll
+    for (int r = 0; r < R2; ++r) x[q * R2 + r] = line[pidx<V>(b + r * (L / R2))];
+  }
+  __syncthreads();
+}
+
+// Stages S .. nst-1 of one transform.  On return x[q RL + r] = out[b + r L/RL]
+// with RL the radix of the last stage.
+template <typename V, int L, int E, int DIR, bool REV, int S>
+__device__ __forceinline__ void col_stages(V (&x)[E], int t, const V* tw, V* line) {
+  constexpr int R = ColPlan<L>::radix(S, REV), NS = ColPlan<L>::ns(S, REV);
+  col_butterflies<V, L, E, DIR, R, NS>(x, t, tw);
+  if constexpr (S + 1 < ColPlan<L>::nst) {
+    col_exchange<V, L, E, R, NS, ColPlan<L>::radix(S + 1, REV)>(x, t, line);
+    col_stages<V, L, E, DIR, REV, S + 1>(x, t, tw, line);
+  }
+}
+
+enum ColMode { COL_Y_FWD = 0, COL_Y_INV = 1, COL_Z = 2 };
+
+// Elements per thread: 16 for the FP32 spectrum at L >= 256 (wider column
+// tiles, more loads in flight per thread), 8 otherwise.  No register cap:
+// capping (to fit more CTAs per SM) measured slower on every length.
+template <typename V, int L, int MODE> struct ColCfg {
+  static constexpr int E = (std::is_same<V, float2>::value && L >= 256) ? 16 : 8;
+};
+
+template <typename V>
+__device__ __forceinline__ typename Real<V>::T table_value(const PipeArgs& a, size_t i) {
+  if constexpr (std::is_same<V, float2>::value) {
+    return a.table32 ? a.table32[i] : d2f_rn(a.table[i]);
+  } else if constexpr (std::is_same<V, dfc>::value) {
+    if (a.tabledf) {
+      const float2 h = a.tabledf[i];
+      return df(h.x, h.y);
+    }
+    return df_of(a.table[i]);
+  } else {
+    return a.table[i];
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ typename Real<V>::T real_of(double v) {
+  if constexpr (std::is_same<V, float2>::value) return d2f_rn(v);
+  else if constexpr (std::is_same<V, dfc>::value) return df_of(v);
+  else return v;
+}
+
+
+template <typename V, int L, int MODE>
+__global__ void __launch_bounds__(kThreads) k_col(PassGeom g, const V* __restrict__ twg, Batch b,
+                                                 PipeArgs a) {
+  constexpr int E = ColCfg<V, L, MODE>::E;
+  constexpr int TPC = L / E, TC = kThreads / TPC, LS = line_stride<V>(L);
+  const int slot = pass_slot<V>(b);
+  if (slot < 0) return;
+  V* __restrict__ W = reinterpret_cast<V*>(a.W) + slot * a.wstride;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* tw = reinterpret_cast<V*>(smem_raw);
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
+  const int c = threadIdx.x % TC, t = threadIdx.x / TC;
+  const int kx = blockIdx.x * TC + c;
+  const bool act = kx < g.Hx;
+  V* line = tw + L + c * LS;
+  size_t stride;
+  V* col;
+  int nload, nstore;
+  if constexpr (MODE == COL_Z) {
+    stride = (size_t)g.Py * g.Hx;
+    col = W + (size_t)blockIdx.y * g.Hx + kx;
+    nload = g.nz;
+    nstore = g.nz;
+  } else {
+    stride = g.Hx;
+    col = W + (size_t)blockIdx.y * g.Py * g.Hx + kx;
+    nload = MODE == COL_Y_FWD ? g.ny : L;    // forward: rows y >= ny are the zero padding
+    nstore = MODE == COL_Y_FWD ? L : g.ny;   // inverse: crop to y < ny
+  }
+  constexpr int R0 = ColPlan<L>::radix(0, false);
+  V x[E];
+#pragma unroll
+  for (int q = 0; q < E / R0; ++q)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int row = t + q * TPC + r * (L / R0);
+      x[q * R0 + r] = (act && row < nload) ? col[(size_t)row * stride] : czero<V>();
+    }
+  __syncthreads();   // twiddles staged
+  col_stages<V, L, E, MODE == COL_Y_INV ? +1 : -1, false, 0>(x, t, tw, line);
+  constexpr int RL = ColPlan<L>::radix(ColPlan<L>::nst - 1, false);
+  if constexpr (MODE == COL_Z) {
+    const int ky = blockIdx.y;
+    const int kyp = min(ky, g.Py - ky);
+    const int hy = g.Py / 2 + 1;
+    const size_t t0 = (size_t)kyp * g.Hx + (act ? kx : 0);
+    const size_t tz = (size_t)hy * g.Hx;
+    const bool use_k0 = a.slot_k0 && b.st && b.st[slot].use_k0;
+    const bool at0 = use_k0 && kx == 0 && ky == 0;
+#pragma unroll
+    for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int kz = t + q * TPC + r * (L / RL);
+        const int kzp = min(kz, L - kz);
+        typename Real<V>::T tv = table_value<V>(a, t0 + (size_t)kzp * tz);
+        if (at0 && kz == 0) tv = real_of<V>(b.st[slot].k0);
+        x[q * RL + r] = cscale(x[q * RL + r], tv);
+      }
+    col_stages<V, L, E, +1, true, 0>(x, t, tw, line);
+    // the reversed transform ends with radix R0
+#pragma unroll
+    for (int q = 0; q < E / R0; ++q)
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        const int row = t + q * TPC + r * (L / R0);
+        if (act && row < nstore) col[(size_t)row * stride] = x[q * R0 + r];
+      }
+  } else {
+#pragma unroll
+    for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int row = t + q * TPC + r * (L / RL);
+        if (act && row < nstore) col[(size_t)row * stride] = x[q * RL + r];
+      }
+  }
+}
+
+template <typename V, int L, int MODE>
+void launch_col_len(const PassGeom& g, const V* tw, const Batch& b, const PipeArgs& a, int nslots,
+                    cudaStream_t st) {
+  constexpr int TC = kThreads / (L / ColCfg<V, L, MODE>::E);
+  const size_t sm = (size_t)(L + TC * line_stride<V>(L)) * sizeof(V);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_col<V, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const dim3 grid((g.Hx + TC - 1) / TC, MODE == COL_Z ? g.Py : g.nz, nslots);
+  count_launch();
+  k_col<V, L, MODE><<<grid, kThreads, sm, st>>>(g, tw, b, a);
+}
+
+template <typename V, int MODE>
+bool launch_col_mode(int L, const PassGeom& g, const V* tw, const Batch& b, const PipeArgs& a,
+                     int nslots, cudaStream_t st) {
+  switch (L) {
+    case 64: launch_col_len<V, 64, MODE>(g, tw, b, a, nslots, st); return true;
+    case 128: launch_col_len<V, 128, MODE>(g, tw, b, a, nslots, st); return true;
+    case 256: launch_col_len<V, 256, MODE>(g, tw, b, a, nslots, st); return true;
+    case 512: launch_col_len<V, 512, MODE>(g, tw, b, a, nslots, st); return true;
+    case 1024: launch_col_len<V, 1024, MODE>(g, tw, b, a, nslots, st); return true;
+    default: return false;
+  }
+}
+
+}  // namespace
+
+bool col_pass_supported(int L) {
+  return L == 64 || L == 128 || L == 256 || L == 512 || L == 1024;
+}
+
+template <typename V>
+bool launch_col_pass(int mode, int L, const PassGeom& g, const V* tw, const Batch& b,
+                     const PipeArgs& a, int nslots, cudaStream_t st) {
+  // The FP64 passes are bound by the FP64 pipe; they keep the shared-memory
+  // kernels, which measured faster for them.
+  if (std::is_same<V, double2>::value) return false;
+  switch (mode) {
+    case COL_Y_FWD: return launch_col_mode<V, COL_Y_FWD>(L, g, tw, b, a, nslots, st);
+    case COL_Y_INV: return launch_col_mode<V, COL_Y_INV>(L, g, tw, b, a, nslots, st);
+    default: return launch_col_mode<V, COL_Z>(L, g, tw, b, a, nslots, st);
+  }
+}
+
+template bool launch_col_pass<double2>(int, int, const PassGeom&, const double2*, const Batch&,
+                                       const PipeArgs&, int, cudaStream_t);
+template bool launch_col_pass<float2>(int, int, const PassGeom&, const float2*, const Batch&,
+                                      const PipeArgs&, int, cudaStream_t);
+template bool launch_col_pass<dfc>(int, int, const PassGeom&, const dfc*, const Batch&,
+                                   const PipeArgs&, int, cudaStream_t);
+
+}  // namespace gps

@@ -156,6 +156,12 @@ void launch_z(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
 template <typename V>
 void launch_x_inv(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
                   const PipeArgs& a, int nslots, cudaStream_t st);
+// Register-resident column passes (fft_col.cu) for power-of-two lengths
+// 64 .. 1024: mode 0 y forward, 1 y inverse, 2 z.  false: length not covered.
+bool col_pass_supported(int L);
+template <typename V>
+bool launch_col_pass(int mode, int L, const PassGeom& g, const V* tw, const Batch& b,
+                     const PipeArgs& a, int nslots, cudaStream_t st);
 size_t x_lines_smem_bytes(int L, int lines, size_t vbytes);
 int x_pass_blocks(const PassGeom& g);
 

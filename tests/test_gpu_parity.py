@@ -115,6 +115,44 @@ def test_precondition_fp32_spectrum(gps, ctx, bc, n, h):
     assert relmax(N(v, g.shape), f.precondition(r)) < 2e-5
 
 
+# Grids whose padded y / z lengths are the powers of two 64 .. 1024 handled by
+# the register-resident column kernels, with column tiles that end ragged
+# (Hx not a multiple of the columns per CTA); free-BC boxes are cubic in
+# length, as the oversampled free kernel requires.
+COLUMN = [
+    (synth.BC_PERIODIC, (20, 64, 128), (0.4, 0.4, 0.3)),    # y 64, z 128
+    (synth.BC_FREE, (16, 32, 64), (0.8, 0.4, 0.2)),         # y 64, z 128 (zero padded)
+    (synth.BC_FREE, (16, 128, 20), (0.8, 0.1, 0.64)),       # y 256
+    (synth.BC_PERIODIC, (12, 256, 512), (0.5, 0.3, 0.2)),   # y 256, z 512
+    (synth.BC_SURFACE, (8, 6, 512), (0.5, 0.5, 0.1)),       # z 1024
+]
+
+
+@pytest.mark.parametrize("bc,n,h", COLUMN)
+def test_vacuum_solve_column_kernels(gps, ctx, bc, n, h):
+    g = _grid(bc, n, h)
+    rng = np.random.default_rng(21)
+    sigma = rng.standard_normal(g.shape)
+    w = T(np.zeros(g.shape))
+    ctx.vacuum_solve(gps.grid_from(g), T(sigma), w)
+    ref = VacuumSolver(g).apply(sigma)
+    assert relmax(N(w, g.shape), ref) < 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("df64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("bc,n,h", COLUMN)
+def test_precondition_column_kernels(gps, ctx, bc, n, h, prec, tol):
+    g = _grid(bc, n, h)
+    rng = np.random.default_rng(22)
+    eps = 1.0 + 30.0 * rng.random(g.shape)
+    r = rng.standard_normal(g.shape)
+    f = Fields(g, eps)
+    v = T(np.zeros(g.shape))
+    code = {"fp64": gps.GPS_FP64, "df64": gps.GPS_DF64, "fp32": gps.GPS_MIXED}[prec]
+    ctx.precondition(gps.grid_from(g), T(f.s), T(r), v, precision=code)
+    assert relmax(N(v, g.shape), f.precondition(r)) < tol
+
+
 def _solve_pair(gps, ctx, p, kind="gpe", tol_rel=1e-13, **okw):
     g = p.grid
     phi = T(np.zeros(g.shape))
