@@ -290,7 +290,9 @@ def run_serving(gps, device, args, count=None):
     """Bounded sample of the serving workload: requests drawn like the
     512-request stream (edges {48,64,96,128,192}, BC and problem mixed,
     5-80 charges, 0.01-1 M), Poisson arrivals at 1.5x the capacity measured
-    by a batch solve of the same requests, 120 GB admission budget."""
+    by a batch solve of the same requests, 120 GB admission budget.  Every
+    request runs the mixed-precision path (FP32 spectrum inside the FP64
+    PCG, FP64 certificate of the result)."""
     import threading
     import synth
     count = count or args.serving_count
@@ -308,7 +310,8 @@ def run_serving(gps, device, args, count=None):
         eps = np.ascontiguousarray(p.eps.ravel())
         phi = np.zeros(p.grid.npts)
         r = gps.make_request(gps.grid_from(p.grid), kind, rho, eps, phi, el,
-                             gps.default_opts(tol_abs=1e-10, tol_outer=1e-10, max_iter=3000))
+                             gps.default_opts(tol_abs=1e-10, tol_outer=1e-10, max_iter=3000,
+                                              precision=gps.GPS_MIXED))
         return r, (rho, eps, phi)
 
     ctx = gps.Context(device, 120 << 30)
@@ -343,7 +346,8 @@ def run_serving(gps, device, args, count=None):
     return {"requests": count, "ok": ok, "arrival_rate_per_s": rate, "batch_capacity_solves_per_s": capacity,
             "solves_per_s": count / wall, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "max_concurrent": stats["max_concurrent"],
-            "pool_bytes": stats["bytes_in_use"]}
+            "pool_bytes": stats["bytes_in_use"], "precision": "mixed (FP32 spectrum, FP64 certificate)",
+            "max_certificate": float(max(rep.fixed_point_res for _, rep in results))}
 
 
 def run_e2e(ctx, g, p, npts, opts, flush, args):
@@ -487,8 +491,45 @@ def run_passes(args):
         ctx.precondition(g, s, r, v, code)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
+    out["cufft"] = cufft_comparison(torch, grid, P, args.steps)
     print(json.dumps(out))
     ctx.close()
+
+
+def cufft_comparison(torch, grid, P, steps):
+    """Timed comparison only (not part of any solve): cuFFT through torch.fft on
+    the same application, v = s irfftn(G rfftn(pad(s r))), in FP64 and FP32.
+    cuFFT transforms the full padded box (it cannot skip the zero padding);
+    the Green's function is a random real array of the half-spectrum shape."""
+    res = {}
+    nx, ny, nz = grid.nx, grid.ny, grid.nz
+    shp = (P["Pz"], P["Py"], P["Px"])
+    for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        try:
+            s = torch.rand((nz, ny, nx), dtype=torch.float64, device="cuda") + 0.1
+            r = torch.randn((nz, ny, nx), dtype=torch.float64, device="cuda")
+            G = torch.rand((P["Pz"], P["Py"], P["Hx"]), dtype=dt, device="cuda")
+            pad = torch.zeros(shp, dtype=dt, device="cuda")
+
+            def apply():
+                pad[:nz, :ny, :nx] = (s * r).to(dt)
+                w = torch.fft.irfftn(torch.fft.rfftn(pad) * G, s=shp)
+                return s * w[:nz, :ny, :nx].to(torch.float64)
+
+            for _ in range(3):
+                apply()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                apply()
+            e1.record()
+            e1.synchronize()
+            res[name] = {"us": round(e0.elapsed_time(e1) / steps * 1e3, 1)}
+            del s, r, G, pad
+            torch.cuda.empty_cache()
+        except Exception as exc:   # e.g. out of memory on a very large box
+            res[name] = {"error": str(exc)[:120]}
+    return res
 
 
 def main():

@@ -336,12 +336,22 @@ void upload_twiddles(Shape* S, int L, double2** t64, float2** t32, dfc** tdf) {
     hdf[m].x = df(cx, (float)(c - (long double)cx));
     hdf[m].y = df(sy, (float)(s - (long double)sy));
   }
+  // FP32 and df64 tables carry, after the plain table, the per-stage layouts
+  // of the register-resident column passes (zeros where L is not served).
+  std::vector<int> idx(2 * (size_t)L, 0);
+  const bool col = col_stage_twiddle_index(L, idx.data());
+  h32.resize(3 * (size_t)L);
+  hdf.resize(3 * (size_t)L);
+  for (size_t i = 0; i < 2 * (size_t)L; ++i) {
+    h32[L + i] = col ? h32[idx[i]] : float2{0.f, 0.f};
+    hdf[L + i] = col ? hdf[idx[i]] : dfc{df(0.f, 0.f), df(0.f, 0.f)};
+  }
   *t64 = S->mem.alloc<double2>(L);
-  *t32 = S->mem.alloc<float2>(L);
-  *tdf = S->mem.alloc<dfc>(L);
+  *t32 = S->mem.alloc<float2>(3 * (size_t)L);
+  *tdf = S->mem.alloc<dfc>(3 * (size_t)L);
   ck(cudaMemcpy(*t64, h64.data(), L * sizeof(double2), cudaMemcpyHostToDevice));
-  ck(cudaMemcpy(*t32, h32.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
-  ck(cudaMemcpy(*tdf, hdf.data(), L * sizeof(dfc), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(*t32, h32.data(), 3 * (size_t)L * sizeof(float2), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(*tdf, hdf.data(), 3 * (size_t)L * sizeof(dfc), cudaMemcpyHostToDevice));
 }
 
 // Free-BC table: h^3 g on the octant from the 4x oversampled truncated-Coulomb

@@ -19,6 +19,7 @@
 #include "fft_common.cuh"
 
 
+
 namespace gps {
 namespace {
 
@@ -38,19 +39,35 @@ template <int L> struct ColPlan {
   }
 };
 
+// Twiddles of the stages, laid out per stage as W[s][r - 1][k] (k < Ns, the
+// factor W_(Ns R)^(r k)), so that the threads of a warp, which hold
+// consecutive k, read consecutive addresses (the index r k L/(Ns R) into the
+// plain table scatters them).  The twiddle array of a length L served here
+// holds three tables of L entries: the plain e^{-2 pi i m/L}, this layout for
+// the forward radix order, and for the reversed order (built once per shape
+// by the engine, col_stage_twiddle_index).  Offset of stage s in the layout:
+template <int L, bool REV>
+__host__ __device__ constexpr int stage_tw_offset(int s) {
+  int o = 0;
+  for (int i = 0; i < s; ++i) o += (ColPlan<L>::radix(i, REV) - 1) * ColPlan<L>::ns(i, REV);
+  return o;
+}
+template <int L, bool REV>
+__host__ __device__ constexpr int stage_tw_size() { return stage_tw_offset<L, REV>(ColPlan<L>::nst); }
+
 // Butterflies of one stage (radix R, Ns = NS) on the thread's E elements:
 // butterfly q is b = t + q L/E with inputs x[q R + r] = in[b + r L/R].
+// tws: this stage's twiddles W[r - 1][k].
 template <typename V, int L, int E, int DIR, int R, int NS>
-__device__ __forceinline__ void col_butterflies(V (&x)[E], int t, const V* tw) {
+__device__ __forceinline__ void col_butterflies(V (&x)[E], int t, const V* tws) {
   constexpr int TPC = L / E, Q = E / R;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     if constexpr (NS > 1) {
-      constexpr int TS = L / (NS * R);
       const int k = (t + q * TPC) & (NS - 1);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const V w = tw[r * k * TS];
+        const V w = tws[(r - 1) * NS + k];
         x[q * R + r] = DIR < 0 ? cmul(x[q * R + r], w) : cmulc(x[q * R + r], w);
       }
     }
@@ -86,7 +103,7 @@ __device__ __forceinline__ void col_exchange(V (&x)[E], int t, V* line) {
 template <typename V, int L, int E, int DIR, bool REV, int S>
 __device__ __forceinline__ void col_stages(V (&x)[E], int t, const V* tw, V* line) {
   constexpr int R = ColPlan<L>::radix(S, REV), NS = ColPlan<L>::ns(S, REV);
-  col_butterflies<V, L, E, DIR, R, NS>(x, t, tw);
+  col_butterflies<V, L, E, DIR, R, NS>(x, t, tw + stage_tw_offset<L, REV>(S));
   if constexpr (S + 1 < ColPlan<L>::nst) {
     col_exchange<V, L, E, R, NS, ColPlan<L>::radix(S + 1, REV)>(x, t, line);
     col_stages<V, L, E, DIR, REV, S + 1>(x, t, tw, line);
@@ -96,10 +113,15 @@ __device__ __forceinline__ void col_stages(V (&x)[E], int t, const V* tw, V* lin
 enum ColMode { COL_Y_FWD = 0, COL_Y_INV = 1, COL_Z = 2 };
 
 // Elements per thread: 16 for the FP32 spectrum at L >= 256 (wider column
-// tiles, more loads in flight per thread), 8 otherwise.  No register cap:
-// capping (to fit more CTAs per SM) measured slower on every length.
+// tiles, more loads in flight per thread), 8 otherwise.
 template <typename V, int L, int MODE> struct ColCfg {
-  static constexpr int E = (std::is_same<V, float2>::value && L >= 256) ? 16 : 8;
+  static constexpr bool f32 = std::is_same<V, float2>::value;
+  static constexpr int E = (f32 && L >= 256) ? 16 : 8;
+  // Resident CTAs per SM asked of the register allocator: 2 (128 registers a
+  // thread) at 16 elements, 3 (85) otherwise.  Measured: the FP32 z pass at
+  // 16 elements takes ~146 registers uncapped, fits one CTA per SM and runs
+  // 1.6x slower; the df64 passes gain 2-3 % from the third CTA.
+  static constexpr int B = (f32 && E == 16) ? 2 : 3;
 };
 
 template <typename V>
@@ -126,7 +148,7 @@ __device__ __forceinline__ typename Real<V>::T real_of(double v) {
 
 
 template <typename V, int L, int MODE>
-__global__ void __launch_bounds__(kThreads) k_col(PassGeom g, const V* __restrict__ twg, Batch b,
+__global__ void __launch_bounds__(kThreads, (ColCfg<V, L, MODE>::B)) k_col(PassGeom g, const V* __restrict__ twg, Batch b,
                                                  PipeArgs a) {
   constexpr int E = ColCfg<V, L, MODE>::E;
   constexpr int TPC = L / E, TC = kThreads / TPC, LS = line_stride<V>(L);
@@ -134,12 +156,12 @@ __global__ void __launch_bounds__(kThreads) k_col(PassGeom g, const V* __restric
   if (slot < 0) return;
   V* __restrict__ W = reinterpret_cast<V*>(a.W) + slot * a.wstride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* tw = reinterpret_cast<V*>(smem_raw);
-  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
+  const V* tw = twg + L;                           // forward-order stage twiddles (global, cached)
+  const V* twr = twg + 2 * L;                      // reversed-order stage twiddles (z inverse)
   const int c = threadIdx.x % TC, t = threadIdx.x / TC;
   const int kx = blockIdx.x * TC + c;
   const bool act = kx < g.Hx;
-  V* line = tw + L + c * LS;
+  V* line = reinterpret_cast<V*>(smem_raw) + c * LS;
   size_t stride;
   V* col;
   int nload, nstore;
@@ -163,7 +185,6 @@ __global__ void __launch_bounds__(kThreads) k_col(PassGeom g, const V* __restric
       const int row = t + q * TPC + r * (L / R0);
       x[q * R0 + r] = (act && row < nload) ? col[(size_t)row * stride] : czero<V>();
     }
-  __syncthreads();   // twiddles staged
   col_stages<V, L, E, MODE == COL_Y_INV ? +1 : -1, false, 0>(x, t, tw, line);
   constexpr int RL = ColPlan<L>::radix(ColPlan<L>::nst - 1, false);
   if constexpr (MODE == COL_Z) {
@@ -184,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) k_col(PassGeom g, const V* __restric
         if (at0 && kz == 0) tv = real_of<V>(b.st[slot].k0);
         x[q * RL + r] = cscale(x[q * RL + r], tv);
       }
-    col_stages<V, L, E, +1, true, 0>(x, t, tw, line);
+    col_stages<V, L, E, +1, true, 0>(x, t, twr, line);
     // the reversed transform ends with radix R0
 #pragma unroll
     for (int q = 0; q < E / R0; ++q)
@@ -208,7 +229,7 @@ template <typename V, int L, int MODE>
 void launch_col_len(const PassGeom& g, const V* tw, const Batch& b, const PipeArgs& a, int nslots,
                     cudaStream_t st) {
   constexpr int TC = kThreads / (L / ColCfg<V, L, MODE>::E);
-  const size_t sm = (size_t)(L + TC * line_stride<V>(L)) * sizeof(V);
+  const size_t sm = (size_t)(TC * line_stride<V>(L)) * sizeof(V);
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_col<V, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const dim3 grid((g.Hx + TC - 1) / TC, MODE == COL_Z ? g.Py : g.nz, nslots);
@@ -233,6 +254,33 @@ bool launch_col_mode(int L, const PassGeom& g, const V* tw, const Batch& b, cons
 
 bool col_pass_supported(int L) {
   return L == 64 || L == 128 || L == 256 || L == 512 || L == 1024;
+}
+
+namespace {
+template <int L>
+void stage_index(int* idx) {
+  for (int rev = 0; rev < 2; ++rev) {
+    int* out = idx + rev * L;
+    for (int i = 0; i < L; ++i) out[i] = 0;
+    for (int s = 0; s < ColPlan<L>::nst; ++s) {
+      const int R = ColPlan<L>::radix(s, rev != 0), NS = ColPlan<L>::ns(s, rev != 0);
+      const int o = rev ? stage_tw_offset<L, true>(s) : stage_tw_offset<L, false>(s);
+      for (int r = 1; r < R; ++r)
+        for (int k = 0; k < NS; ++k) out[o + (r - 1) * NS + k] = r * k * (L / (NS * R));
+    }
+  }
+}
+}  // namespace
+
+bool col_stage_twiddle_index(int L, int* idx) {
+  switch (L) {
+    case 64: stage_index<64>(idx); return true;
+    case 128: stage_index<128>(idx); return true;
+    case 256: stage_index<256>(idx); return true;
+    case 512: stage_index<512>(idx); return true;
+    case 1024: stage_index<1024>(idx); return true;
+    default: return false;
+  }
 }
 
 template <typename V>

@@ -157,8 +157,12 @@ template <typename V>
 void launch_x_inv(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
                   const PipeArgs& a, int nslots, cudaStream_t st);
 // Register-resident column passes (fft_col.cu) for power-of-two lengths
-// 64 .. 1024: mode 0 y forward, 1 y inverse, 2 z.  false: length not covered.
+// 64 .. 1024: mode 0 y forward, 1 y inverse, 2 z.  false: length not covered
+// (and always for the FP64 spectrum).  Their twiddle array `tw` must hold
+// 3 L entries: the plain table and the two per-stage layouts whose plain
+// indices col_stage_twiddle_index(L, idx[2 L]) writes (forward, reversed).
 bool col_pass_supported(int L);
+bool col_stage_twiddle_index(int L, int* idx);
 template <typename V>
 bool launch_col_pass(int mode, int L, const PassGeom& g, const V* tw, const Batch& b,
                      const PipeArgs& a, int nslots, cudaStream_t st);

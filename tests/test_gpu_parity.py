@@ -332,6 +332,48 @@ def test_full_surface_lpb(gps, ctx):
     assert _fixed_point_residual(p, N(phi, p.grid.shape), lam=lam) < 1e-9
 
 
+def test_full_surface_nlpb(gps, ctx):
+    """Config-3 slab with the nonlinear PB term (0.1 M, Newton outer loop),
+    FP64 at full size: the oracle's fixed-point residual of the full
+    nonlinear equation at the GPU potential."""
+    p = synth.workload(3, kind="nlpb")
+    el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.pb_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), el, "nlpb", phi,
+                       gps.default_opts(tol_outer=1e-10, max_iter=2000))
+    assert rep.status == 0 and rep.outer_iters > 1
+    ph = N(phi, p.grid.shape)
+    gam = oracle.pb.exclusion_from_eps(p.eps, p.eps0)
+    rions = oracle.pb.ionic_charge(ph, gam, p.electrolyte)
+    assert _fixed_point_residual(p, ph, rions=rions) < 1e-9
+
+
+def test_full_free_union_nlpb_mixed(gps, ctx):
+    """Config 4 at full size: free 256^3, 200 charges in a union-of-spheres
+    cavity, nonlinear PB at 0.5 M, FP32 spectrum after the switch with the
+    double-float spectrum as the high-precision side.  The FP64 certificate
+    and the oracle's fixed-point residual of the full nonlinear equation are
+    below 1e-8, and the result agrees with an all-double-float solve to 1e-8."""
+    p = synth.workload(4)
+    el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+    g = gps.grid_from(p.grid)
+    rho, eps = T(p.rho), T(p.eps)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.pb_solve(g, rho, eps, el, "nlpb", phi,
+                       gps.default_opts(tol_outer=1e-10, max_iter=3000, precision=gps.GPS_MIXED_DF64))
+    assert rep.status == 0
+    assert 0 <= rep.fixed_point_res < 1e-8
+    ref = T(np.zeros(p.grid.shape))
+    rep_ref = ctx.pb_solve(g, rho, eps, el, "nlpb", ref,
+                           gps.default_opts(tol_outer=1e-10, max_iter=3000, precision=gps.GPS_DF64))
+    assert rep_ref.status == 0
+    ph, ph_ref = N(phi, p.grid.shape), N(ref, p.grid.shape)
+    assert rel2(ph, ph_ref) <= 1e-8
+    gam = oracle.pb.exclusion_from_eps(p.eps, p.eps0)
+    rions = oracle.pb.ionic_charge(ph, gam, p.electrolyte)
+    assert _fixed_point_residual(p, ph, rions=rions) < 1e-8
+
+
 # ------------------------------------------------------ mixed precision -----
 
 @pytest.mark.parametrize("wl,kw,kind", [
