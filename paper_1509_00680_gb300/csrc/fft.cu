@@ -162,31 +162,6 @@ __device__ __forceinline__ void pair_offsets(const PassGeom& g, int p0, int nl, 
   }
 }
 
-// Input value of the x pass: in * scale, rounded to the spectrum's real type.
-// The FP32 spectrum multiplies in FP32 unless the FP64 sum of the products is
-// wanted; conversions run on the integer pipe.
-template <typename V>
-__device__ __forceinline__ typename Real<V>::T load_scaled(const double* in, const double* scale,
-                                                           size_t o, bool red, double& sum) {
-  if constexpr (std::is_same<V, float2>::value) {
-    if (red) {
-      double v = in[o];
-      if (scale) v *= scale[o];
-      sum += v;
-      return d2f_rn(v);
-    }
-    float v = d2f_rn(in[o]);
-    if (scale) v *= d2f_rn(scale[o]);
-    return v;
-  } else {
-    double v = in[o];
-    if (scale) v *= scale[o];
-    if (red) sum += v;
-    if constexpr (std::is_same<V, dfc>::value) return df_of(v);
-    else return v;
-  }
-}
-
 template <typename V>
 __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, const V* __restrict__ twg,
                                                    Batch b, PipeArgs a) {
@@ -364,30 +339,6 @@ __global__ void __launch_bounds__(kThreads) k_z(PassGeom g, FftSched s, const V*
   }
 }
 
-// Real output value of the x inverse pass as a double (integer-pipe
-// conversions; the FP32 spectrum scales in FP32).
-template <typename V>
-__device__ __forceinline__ double out_value(typename Real<V>::T z, const double* scale, size_t o) {
-  if constexpr (std::is_same<V, float2>::value) {
-    float v = z;
-    if (scale) v *= d2f_rn(scale[o]);
-    return f2d(v);
-  } else {
-    double v;
-    if constexpr (std::is_same<V, dfc>::value) v = dbl_of(z);
-    else v = z;
-    if (scale) v *= scale[o];
-    return v;
-  }
-}
-
-template <typename V>
-__device__ __forceinline__ double unscaled(typename Real<V>::T z) {
-  if constexpr (std::is_same<V, float2>::value) return f2d(z);
-  else if constexpr (std::is_same<V, dfc>::value) return dbl_of(z);
-  else return z;
-}
-
 template <typename V>
 __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, const V* __restrict__ twg,
                                                    Batch b, PipeArgs a) {
@@ -493,6 +444,7 @@ static void set_smem(K kernel, size_t bytes) {
 template <typename V>
 void launch_x_fwd(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
                   const PipeArgs& a, int nslots, cudaStream_t st) {
+  if (launch_xr_pass<V>(false, s.L, g, tw, b, a, nslots, st)) return;
   const size_t sm = x_lines_smem_bytes(s.L, g.lines_x, sizeof(V));
   set_smem(k_x_fwd<V>, sm);
   count_launch();
@@ -529,6 +481,7 @@ void launch_z(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
 template <typename V>
 void launch_x_inv(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
                   const PipeArgs& a, int nslots, cudaStream_t st) {
+  if (launch_xr_pass<V>(true, s.L, g, tw, b, a, nslots, st)) return;
   const size_t sm = x_lines_smem_bytes(s.L, g.lines_x, sizeof(V));
   set_smem(k_x_inv<V>, sm);
   count_launch();

@@ -113,7 +113,7 @@ __device__ __forceinline__ void col_stages(V (&x)[E], int t, const V* tw, V* lin
 enum ColMode { COL_Y_FWD = 0, COL_Y_INV = 1, COL_Z = 2 };
 
 // Elements per thread: 16 for the FP32 spectrum at L >= 256 (wider column
-// tiles, more loads in flight per thread), 8 otherwise.
+// tiles, more loads in flight per thread), 8 otherwise.  MODE 3: x passes.
 template <typename V, int L, int MODE> struct ColCfg {
   static constexpr bool f32 = std::is_same<V, float2>::value;
   static constexpr int E = (f32 && L >= 256) ? 16 : 8;
@@ -250,7 +250,188 @@ bool launch_col_mode(int L, const PassGeom& g, const V* tw, const Batch& b, cons
   }
 }
 
+// ---- register-resident x passes -----------------------------------------
+// Lines are row pairs: two real rows of length nx, zero-padded to L = Px, as
+// one complex transform (two-for-one real FFT).  A CTA transforms NL =
+// 256 / (L/E) pairs; thread t of a pair holds elements t + q L/E + r L/R, so
+// consecutive threads read and write consecutive elements of a row.
+
+template <typename V, int L>
+__global__ void __launch_bounds__(kThreads, (ColCfg<V, L, 3>::B)) k_xr_fwd(PassGeom g, const V* __restrict__ twg,
+                                                                         Batch b, PipeArgs a) {
+  using T = typename Real<V>::T;
+  constexpr int E = ColCfg<V, L, 3>::E;
+  constexpr int TPC = L / E, NL = kThreads / TPC, LS = line_stride<V>(L);
+  const int slot = pass_slot<V>(b);
+  if (slot < 0) return;
+  const double* __restrict__ in = a.in + slot * b.vstride;
+  const double* __restrict__ scale = a.in_scale ? a.in_scale + slot * b.vstride : nullptr;
+  V* __restrict__ W = reinterpret_cast<V*>(a.W) + slot * a.wstride;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int l = threadIdx.x / TPC, t = threadIdx.x % TPC;
+  V* line = reinterpret_cast<V*>(smem_raw) + l * LS;
+  const int npairs = (g.nrows + 1) >> 1;
+  const int pr = blockIdx.x * NL + l;
+  const bool act = pr < npairs;
+  const int ra = 2 * pr;
+  const bool hasb = act && ra + 1 < g.nrows;
+  const bool red = a.red_mu && b.st;
+  double sum = 0.0;
+  constexpr int R0 = ColPlan<L>::radix(0, false);
+  V x[E];
+#pragma unroll
+  for (int q = 0; q < E / R0; ++q)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int j = t + q * TPC + r * (L / R0);
+      T va = T(0), vb = T(0);
+      if (act && j < g.nx) {
+        const size_t o = (size_t)ra * g.nx + j;
+        va = load_scaled<V>(in, scale, o, red, sum);
+        if (hasb) vb = load_scaled<V>(in, scale, o + g.nx, red, sum);
+      }
+      x[q * R0 + r] = mk<V>(va, vb);
+    }
+  col_stages<V, L, E, -1, false, 0>(x, t, twg + L, line);
+  // Z in natural order; Z_k and Z_(L-k) meet through the line
+  constexpr int RL = ColPlan<L>::radix(ColPlan<L>::nst - 1, false);
+#pragma unroll
+  for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) line[pidx<V>(t + q * TPC + r * (L / RL))] = x[q * RL + r];
+  __syncthreads();
+  if (act) {
+    V* wa = W + row_offset(g, ra);
+    V* wb = hasb ? W + row_offset(g, ra + 1) : nullptr;
+    const T half = T(0.5);
+    for (int k = t; k < g.Hx; k += TPC) {
+      const V zk = line[pidx<V>(k)];
+      const V zm = line[pidx<V>(k == 0 ? 0 : L - k)];
+      // A_k = (Z_k + conj Z_(L-k))/2 ; B_k = -i (Z_k - conj Z_(L-k))/2
+      wa[k] = mk<V>(half * (zk.x + zm.x), half * (zk.y - zm.y));
+      if (hasb) wb[k] = mk<V>(half * (zk.y + zm.y), half * (zm.x - zk.x));
+    }
+  }
+  if (red)
+    grid_reduce(sum, b.partials + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_MU], &b.st[slot].mu_sum);
+}
+
+template <typename V, int L>
+__global__ void __launch_bounds__(kThreads, (ColCfg<V, L, 3>::B)) k_xr_inv(PassGeom g, const V* __restrict__ twg,
+                                                                         Batch b, PipeArgs a) {
+  using T = typename Real<V>::T;
+  constexpr int E = ColCfg<V, L, 3>::E;
+  constexpr int TPC = L / E, NL = kThreads / TPC, LS = line_stride<V>(L);
+  const int slot = pass_slot<V>(b);
+  if (slot < 0) return;
+  const V* __restrict__ W = reinterpret_cast<const V*>(a.W) + slot * a.wstride;
+  double* __restrict__ out = a.out + slot * b.vstride;
+  const double* __restrict__ out_scale = a.out_scale ? a.out_scale + slot * b.vstride : nullptr;
+  const double* __restrict__ dot_with = a.dot_with ? a.dot_with + slot * b.vstride : nullptr;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int l = threadIdx.x / TPC, t = threadIdx.x % TPC;
+  V* line = reinterpret_cast<V*>(smem_raw) + l * LS;
+  const int npairs = (g.nrows + 1) >> 1;
+  const int pr = blockIdx.x * NL + l;
+  const bool act = pr < npairs;
+  const int ra = 2 * pr;
+  const bool hasb = act && ra + 1 < g.nrows;
+  const V* wa = act ? W + row_offset(g, ra) : W;
+  const V* wb = hasb ? W + row_offset(g, ra + 1) : W;
+  constexpr int R0 = ColPlan<L>::radix(0, false);
+  V x[E];
+#pragma unroll
+  for (int q = 0; q < E / R0; ++q)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int k = t + q * TPC + r * (L / R0);
+      V A = czero<V>(), B = czero<V>();
+      if (act) {
+        if (k < g.Hx) {
+          A = wa[k];
+          if (hasb) B = wb[k];
+          if (k == 0 || 2 * k == L) { A.y = T(0); B.y = T(0); }   // DC and Nyquist are real
+        } else {
+          A = cconj(wa[L - k]);
+          if (hasb) B = cconj(wb[L - k]);
+        }
+      }
+      x[q * R0 + r] = mk<V>(A.x - B.y, A.y + B.x);   // Z = A + i B
+    }
+  col_stages<V, L, E, +1, false, 0>(x, t, twg + L, line);
+  constexpr int RL = ColPlan<L>::radix(ColPlan<L>::nst - 1, false);
+  const bool want_wsum = a.red_wsum && b.st && b.st[slot].gauge;
+  double dot = 0.0, wsum = 0.0;
+#pragma unroll
+  for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int j = t + q * TPC + r * (L / RL);
+      if (act && j < g.nx) {
+        const V zz = x[q * RL + r];
+        const size_t oa = (size_t)ra * g.nx + j;
+        const double va = out_value<V>(zz.x, out_scale, oa);
+        out[oa] = va;
+        if (dot_with) dot += va * dot_with[oa];
+        if (want_wsum) wsum += unscaled<V>(zz.x);
+        if (hasb) {
+          const size_t ob = oa + g.nx;
+          const double vb = out_value<V>(zz.y, out_scale, ob);
+          out[ob] = vb;
+          if (dot_with) dot += vb * dot_with[ob];
+          if (want_wsum) wsum += unscaled<V>(zz.y);
+        }
+      }
+    }
+  if (dot_with && b.st)
+    grid_reduce(dot, b.partials + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_VR], &b.st[slot].vr);
+  if (want_wsum)
+    grid_reduce(wsum, b.partials2 + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_WSUM],
+                &b.st[slot].wsum);
+}
+
+template <typename V, int L>
+void launch_xr_len(bool inverse, const PassGeom& g, const V* tw, const Batch& b, const PipeArgs& a,
+                   int nslots, cudaStream_t st) {
+  constexpr int NL = kThreads / (L / ColCfg<V, L, 3>::E);
+  const size_t sm = (size_t)(NL * line_stride<V>(L)) * sizeof(V);
+  const int npairs = (g.nrows + 1) / 2;
+  const dim3 grid((npairs + NL - 1) / NL, 1, nslots);
+  count_launch();
+  if (inverse) {
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_xr_inv<V, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_xr_inv<V, L><<<grid, kThreads, sm, st>>>(g, tw, b, a);
+  } else {
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_xr_fwd<V, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_xr_fwd<V, L><<<grid, kThreads, sm, st>>>(g, tw, b, a);
+  }
+}
+
 }  // namespace
+
+template <typename V>
+bool launch_xr_pass(bool inverse, int L, const PassGeom& g, const V* tw, const Batch& b,
+                    const PipeArgs& a, int nslots, cudaStream_t st) {
+  // Measured: faster for the df64 spectrum only.  The FP64 x passes are
+  // bound by the FP64 pipe and the FP32 ones by their FP64 input / output
+  // handling; both keep the shared-memory kernels.
+  if (!std::is_same<V, dfc>::value) return false;
+  switch (L) {
+    case 64: launch_xr_len<V, 64>(inverse, g, tw, b, a, nslots, st); return true;
+    case 128: launch_xr_len<V, 128>(inverse, g, tw, b, a, nslots, st); return true;
+    case 256: launch_xr_len<V, 256>(inverse, g, tw, b, a, nslots, st); return true;
+    case 512: launch_xr_len<V, 512>(inverse, g, tw, b, a, nslots, st); return true;
+    case 1024: launch_xr_len<V, 1024>(inverse, g, tw, b, a, nslots, st); return true;
+    default: return false;
+  }
+}
+
+template bool launch_xr_pass<double2>(bool, int, const PassGeom&, const double2*, const Batch&,
+                                      const PipeArgs&, int, cudaStream_t);
+template bool launch_xr_pass<float2>(bool, int, const PassGeom&, const float2*, const Batch&,
+                                     const PipeArgs&, int, cudaStream_t);
+template bool launch_xr_pass<dfc>(bool, int, const PassGeom&, const dfc*, const Batch&,
+                                  const PipeArgs&, int, cudaStream_t);
 
 bool col_pass_supported(int L) {
   return L == 64 || L == 128 || L == 256 || L == 512 || L == 1024;

@@ -135,4 +135,53 @@ __device__ __forceinline__ int pass_slot(const Batch& b) {
   return s;
 }
 
+// Input value of the x pass: in * scale, rounded to the spectrum's real type.
+// The FP32 spectrum multiplies in FP32 unless the FP64 sum of the products is
+// wanted; conversions run on the integer pipe.
+template <typename V>
+__device__ __forceinline__ typename Real<V>::T load_scaled(const double* in, const double* scale,
+                                                           size_t o, bool red, double& sum) {
+  if constexpr (std::is_same<V, float2>::value) {
+    if (red) {
+      double v = in[o];
+      if (scale) v *= scale[o];
+      sum += v;
+      return d2f_rn(v);
+    }
+    float v = d2f_rn(in[o]);
+    if (scale) v *= d2f_rn(scale[o]);
+    return v;
+  } else {
+    double v = in[o];
+    if (scale) v *= scale[o];
+    if (red) sum += v;
+    if constexpr (std::is_same<V, dfc>::value) return df_of(v);
+    else return v;
+  }
+}
+
+// Real output value of the x inverse pass as a double (integer-pipe
+// conversions; the FP32 spectrum scales in FP32).
+template <typename V>
+__device__ __forceinline__ double out_value(typename Real<V>::T z, const double* scale, size_t o) {
+  if constexpr (std::is_same<V, float2>::value) {
+    float v = z;
+    if (scale) v *= d2f_rn(scale[o]);
+    return f2d(v);
+  } else {
+    double v;
+    if constexpr (std::is_same<V, dfc>::value) v = dbl_of(z);
+    else v = z;
+    if (scale) v *= scale[o];
+    return v;
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ double unscaled(typename Real<V>::T z) {
+  if constexpr (std::is_same<V, float2>::value) return f2d(z);
+  else if constexpr (std::is_same<V, dfc>::value) return dbl_of(z);
+  else return z;
+}
+
 }  // namespace gps

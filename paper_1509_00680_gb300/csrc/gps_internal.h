@@ -163,6 +163,11 @@ void launch_x_inv(const PassGeom& g, const FftSched& s, const V* tw, const Batch
 // indices col_stage_twiddle_index(L, idx[2 L]) writes (forward, reversed).
 bool col_pass_supported(int L);
 bool col_stage_twiddle_index(int L, int* idx);
+// Register-resident x passes (same lengths and twiddle requirement; used
+// for the df64 spectrum).
+template <typename V>
+bool launch_xr_pass(bool inverse, int L, const PassGeom& g, const V* tw, const Batch& b,
+                    const PipeArgs& a, int nslots, cudaStream_t st);
 template <typename V>
 bool launch_col_pass(int mode, int L, const PassGeom& g, const V* tw, const Batch& b,
                      const PipeArgs& a, int nslots, cudaStream_t st);

@@ -115,8 +115,8 @@ def test_precondition_fp32_spectrum(gps, ctx, bc, n, h):
     assert relmax(N(v, g.shape), f.precondition(r)) < 2e-5
 
 
-# Grids whose padded y / z lengths are the powers of two 64 .. 1024 handled by
-# the register-resident column kernels, with column tiles that end ragged
+# Grids whose padded x / y / z lengths are the powers of two 64 .. 1024 handled
+# by the register-resident kernels, with column tiles that end ragged
 # (Hx not a multiple of the columns per CTA); free-BC boxes are cubic in
 # length, as the oversampled free kernel requires.
 COLUMN = [
@@ -125,6 +125,13 @@ COLUMN = [
     (synth.BC_FREE, (16, 128, 20), (0.8, 0.1, 0.64)),       # y 256
     (synth.BC_PERIODIC, (12, 256, 512), (0.5, 0.3, 0.2)),   # y 256, z 512
     (synth.BC_SURFACE, (8, 6, 512), (0.5, 0.5, 0.1)),       # z 1024
+    # x passes (row pairs; odd row counts leave a last pair with one row)
+    (synth.BC_PERIODIC, (64, 6, 6), (0.3, 0.5, 0.6)),       # x 64
+    (synth.BC_FREE, (32, 5, 9), (0.4, 2.56, 1.42)),         # x 64 (zero padded), 45 rows
+    (synth.BC_PERIODIC, (128, 12, 10), (0.3, 0.4, 0.5)),    # x 128
+    (synth.BC_FREE, (128, 16, 20), (0.1, 0.8, 0.64)),       # x 256
+    (synth.BC_PERIODIC, (512, 6, 8), (0.05, 0.5, 0.5)),     # x 512
+    (synth.BC_SURFACE, (1024, 4, 6), (0.05, 0.5, 0.5)),     # x 1024
 ]
 
 
