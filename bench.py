@@ -143,6 +143,21 @@ def kernel_flops(kind, P):
     return {"update_p": 10.0, "update_r": 6.0}.get(kind, 0.0) * n
 
 
+def reduce_over_ranks(total_ms, units, device=None):
+    """Whole-job numbers of a replica run: the slowest rank's timed region
+    (max over ranks) and the units every rank processed (sum over ranks).
+    The identity on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_ms, units
+    tmax = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    usum = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(usum, op=dist.ReduceOp.SUM)
+    return float(tmax.item()), float(usum.item())
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_1509_00680_gb300 import build
@@ -205,13 +220,7 @@ def run_ours(args, ws, rank, local):
     prof = ctx.get_profile(reset=True)
     ctx.set_profiling(None)
     clk = clocks.stop()
-    total_ms = sum(t_steps)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units = npts * sum(iters) * ws
+    total_ms, units = reduce_over_ranks(sum(t_steps), npts * sum(iters), dev)
     value = units / (total_ms / 1e3)
 
     e2e = None
