@@ -499,7 +499,8 @@ struct Pool {
 
 size_t slot_bytes(const Shape& S) {
   const size_t wn = (size_t)S.Hx * S.Py * S.grid.nz;
-  return 18 * S.n * sizeof(double) + wn * (sizeof(double2) + sizeof(float2)) + 3 * 4096 * sizeof(double);
+  return 18 * S.n * sizeof(double) + S.n * sizeof(float) + wn * (sizeof(double2) + sizeof(float2)) +
+         3 * 4096 * sizeof(double);
 }
 
 std::unique_ptr<Pool> make_pool(std::shared_ptr<Shape> shape, int cap, bool own_stream) {
@@ -515,6 +516,7 @@ std::unique_ptr<Pool> make_pool(std::shared_ptr<Shape> shape, int cap, bool own_
   P->own_eps = f.eps = P->mem.alloc<double>(N);
   P->own_phi = f.phi = P->mem.alloc<double>(N);
   f.s = P->mem.alloc<double>(N);
+  f.s32 = P->mem.alloc<float>(N);
   f.sq = P->mem.alloc<double>(N);
   f.q = P->mem.alloc<double>(N);
   f.qlam = P->mem.alloc<double>(N);
@@ -793,6 +795,8 @@ void launch_round(Pool& P, int m, bool setup, bool init, cudaStream_t st) {
   it.slot_k0 = 1;
   it.red_mu = periodic;
   it.red_wsum = periodic;
+  it.in_scale32 = f.s32;
+  it.out_scale32 = f.s32;
   const Batch bi64 = batch_of(P, PH_ITER, SPEC_FP64), bi32 = batch_of(P, PH_ITER, SPEC_FP32);
   const Batch bidf = batch_of(P, PH_ITER, SPEC_DF64);
   const Batch bi = batch_of(P, PH_ITER, -1);

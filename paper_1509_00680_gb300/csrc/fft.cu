@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, cons
   if (slot < 0) return;
   const double* __restrict__ in = a.in + slot * b.vstride;
   const double* __restrict__ scale = a.in_scale ? a.in_scale + slot * b.vstride : nullptr;
+  const float* __restrict__ scale32 = a.in_scale32 ? a.in_scale32 + slot * b.vstride : nullptr;
   V* __restrict__ W = reinterpret_cast<V*>(a.W) + slot * a.wstride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ size_t woff[2 * kMaxLinesX];
@@ -200,8 +201,8 @@ __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, cons
           const int ra = 2 * (p0 + l);
           if (j < g.nx) {
             const size_t oa = (size_t)ra * g.nx + j;
-            va[u] = load_scaled<V>(in, scale, oa, red, sum);
-            if (ra + 1 < g.nrows) vb[u] = load_scaled<V>(in, scale, oa + g.nx, red, sum);
+            va[u] = load_scaled<V>(in, scale, oa, red, sum, scale32);
+            if (ra + 1 < g.nrows) vb[u] = load_scaled<V>(in, scale, oa + g.nx, red, sum, scale32);
           }
           dst[u] = l * ls + pidx<V>(j);
           it.next();
@@ -348,6 +349,7 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
   const V* __restrict__ W = reinterpret_cast<const V*>(a.W) + slot * a.wstride;
   double* __restrict__ out = a.out + slot * b.vstride;
   const double* __restrict__ out_scale = a.out_scale ? a.out_scale + slot * b.vstride : nullptr;
+  const float* __restrict__ out_scale32 = a.out_scale32 ? a.out_scale32 + slot * b.vstride : nullptr;
   const double* __restrict__ dot_with = a.dot_with ? a.dot_with + slot * b.vstride : nullptr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ size_t woff[2 * kMaxLinesX];
@@ -404,13 +406,13 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
     const int ra = 2 * (p0 + l);
     const V zz = res[l * ls + pidx<V>(j)];
     const size_t oa = (size_t)ra * g.nx + j;
-    const double va = out_value<V>(zz.x, out_scale, oa);
+    const double va = out_value<V>(zz.x, out_scale, oa, out_scale32);
     out[oa] = va;
     if (dot_with) dot += va * dot_with[oa];
     if (want_wsum) wsum += unscaled<V>(zz.x);
     if (ra + 1 < g.nrows) {
       const size_t ob = oa + g.nx;
-      const double vb = out_value<V>(zz.y, out_scale, ob);
+      const double vb = out_value<V>(zz.y, out_scale, ob, out_scale32);
       out[ob] = vb;
       if (dot_with) dot += vb * dot_with[ob];
       if (want_wsum) wsum += unscaled<V>(zz.y);

@@ -140,7 +140,8 @@ __device__ __forceinline__ int pass_slot(const Batch& b) {
 // wanted; conversions run on the integer pipe.
 template <typename V>
 __device__ __forceinline__ typename Real<V>::T load_scaled(const double* in, const double* scale,
-                                                           size_t o, bool red, double& sum) {
+                                                           size_t o, bool red, double& sum,
+                                                           const float* scale32 = nullptr) {
   if constexpr (std::is_same<V, float2>::value) {
     if (red) {
       double v = in[o];
@@ -149,7 +150,8 @@ __device__ __forceinline__ typename Real<V>::T load_scaled(const double* in, con
       return d2f_rn(v);
     }
     float v = d2f_rn(in[o]);
-    if (scale) v *= d2f_rn(scale[o]);
+    if (scale32) v *= scale32[o];
+    else if (scale) v *= d2f_rn(scale[o]);
     return v;
   } else {
     double v = in[o];
@@ -163,10 +165,12 @@ __device__ __forceinline__ typename Real<V>::T load_scaled(const double* in, con
 // Real output value of the x inverse pass as a double (integer-pipe
 // conversions; the FP32 spectrum scales in FP32).
 template <typename V>
-__device__ __forceinline__ double out_value(typename Real<V>::T z, const double* scale, size_t o) {
+__device__ __forceinline__ double out_value(typename Real<V>::T z, const double* scale, size_t o,
+                                            const float* scale32 = nullptr) {
   if constexpr (std::is_same<V, float2>::value) {
     float v = z;
-    if (scale) v *= d2f_rn(scale[o]);
+    if (scale32) v *= scale32[o];
+    else if (scale) v *= d2f_rn(scale[o]);
     return f2d(v);
   } else {
     double v;

@@ -116,6 +116,8 @@ struct Batch {
 struct PipeArgs {
   const double* in;         // x_fwd input
   const double* in_scale;   // optional factor (s)
+  const float* in_scale32;  // optional: in_scale rounded to float, for the FP32 spectrum
+  const float* out_scale32; // optional: out_scale rounded to float, for the FP32 spectrum
   double* out;              // x_inv output
   const double* out_scale;  // optional factor (s or sqrt(eps))
   const double* dot_with;   // optional: reduce (out, dot_with) into st.vr

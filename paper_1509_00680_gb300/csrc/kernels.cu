@@ -92,6 +92,7 @@ __global__ void k_setup_s(Batch b, Fields f, size_t n) {
   SLOT_PROLOGUE(b)
   const double* eps = f.eps + off;
   double* s = f.s + off;
+  float* s32 = f.s32 ? f.s32 + off : nullptr;
   double* sq = f.sq + off;
   double acc = 0.0;
   int bad = 0;
@@ -100,7 +101,9 @@ __global__ void k_setup_s(Batch b, Fields f, size_t n) {
     if (!(e > 0.0)) bad = 1;
     const double r = sqrt(e);
     sq[i] = r;
-    s[i] = 1.0 / r;
+    const double si = 1.0 / r;
+    s[i] = si;
+    if (s32) s32[i] = (float)si;
     acc += e;
   }
   if (bad) S.bad_eps = 1;

@@ -21,6 +21,7 @@ struct Fields {
   double *r, *p, *Ap, *v;                // PCG vectors
   double *rions, *rp, *fresh, *lam, *dphi, *src;   // Algorithm 4
   double *tmp;                           // certificate source
+  float *s32;                            // eps^-1/2 rounded to float (FP32 spectrum passes)
 };
 
 int vec_blocks(size_t n, int nslots);
