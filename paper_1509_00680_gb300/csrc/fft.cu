@@ -130,13 +130,13 @@ constexpr int kMaxLinesX = 64;
 // stores go through generic pointers that the compiler must assume may alias
 // the loads, so without batching each thread would keep a single HBM load in
 // flight.
-template <typename V> struct Batch_ { static constexpr int v = sizeof(V) == 8 ? 8 : 4; };
+template <typename V> struct LoadBatch { static constexpr int v = sizeof(V) == 8 ? 8 : 4; };
 
 // line[pidx(y)] = y < nload ? col[y * stride] : 0 for y = y0, y0 + ystep, ... < L.
 template <typename V>
 __device__ __forceinline__ void load_column(V* line, const V* __restrict__ col, size_t stride, int y0,
                                             int ystep, int L, int nload) {
-  constexpr int U = Batch_<V>::v;
+  constexpr int U = LoadBatch<V>::v;
   for (int yb = y0; yb < L; yb += U * ystep) {
     V v[U];
 #pragma unroll
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
   pair_offsets<V>(g, p0, nl, woff);
   __syncthreads();
   {
-    constexpr int U = Batch_<V>::v / 2;
+    constexpr int U = LoadBatch<V>::v / 2;
     LineIter it(L);
     while (it.l < nl) {
       V A[U], B[U];
