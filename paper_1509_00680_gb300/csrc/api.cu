@@ -646,13 +646,19 @@ float time_launch(F&& launch, cudaStream_t st) {
   return best;
 }
 
-std::vector<int> batch_candidates(int b0, int L, size_t vbytes) {
+// Lines (x passes) or columns (y, z passes) per CTA to try: every count from
+// 1 to 16 that fits in shared memory.  Counts that are not powers of two
+// matter: they set how full the last wave of CTAs is (at 128^3 the power-of-
+// two choices leave 1.7-1.9 waves).  fixed: the pass runs a kernel with its
+// own tiling (register-resident kernels), so only the heuristic is kept.
+std::vector<int> batch_candidates(int b0, int L, size_t vbytes, bool fixed) {
   std::vector<int> c;
-  for (int b : {b0 / 2, b0, 2 * b0, 4 * b0}) {
-    if (b < 1 || b > 64) continue;
-    if (x_lines_smem_bytes(L, b, vbytes) > 220 * 1024) continue;
-    if (std::find(c.begin(), c.end(), b) == c.end()) c.push_back(b);
+  if (fixed) {
+    c.push_back(b0 < 1 ? 1 : b0);
+    return c;
   }
+  for (int b = 1; b <= 16; ++b)
+    if (x_lines_smem_bytes(L, b, vbytes) <= 220 * 1024) c.push_back(b);
   if (c.empty()) c.push_back(1);
   return c;
 }
@@ -700,10 +706,15 @@ void tune_spec(Shape& S, cudaStream_t st) {
     best.fx = S.fx;
     best.fy = S.fy;
     best.fz = S.fz;
+    // passes served by the register-resident kernels (fixed tiling, compile-time radix plan)
+    const bool f64 = std::is_same<V, double2>::value;
+    const bool fixx = std::is_same<V, dfc>::value && col_pass_supported(S.Px);
+    const bool fixy = !f64 && col_pass_supported(S.Py);
+    const bool fixz = !f64 && col_pass_supported(S.Pz);
     // x passes: lines per CTA and radix order of Px
     float tbest = 1e30f;
-    for (int lines : batch_candidates(S.g.lines_x, S.Px, sizeof(V)))
-      for (int order = 0; order < 3; ++order) {
+    for (int lines : batch_candidates(S.g.lines_x, S.Px, sizeof(V), fixx))
+      for (int order = 0; order < (fixx ? 1 : 3); ++order) {
         PassGeom g = best.g;
         g.lines_x = lines;
         FftSched fx;
@@ -713,8 +724,8 @@ void tune_spec(Shape& S, cudaStream_t st) {
         if (t < tbest) { tbest = t; best.g.lines_x = lines; best.fx = fx; }
       }
     tbest = 1e30f;
-    for (int tile : batch_candidates(S.g.tile_y, S.Py, sizeof(V)))
-      for (int order = 0; order < 3; ++order) {
+    for (int tile : batch_candidates(S.g.tile_y, S.Py, sizeof(V), fixy))
+      for (int order = 0; order < (fixy ? 1 : 3); ++order) {
         PassGeom g = best.g;
         g.tile_y = tile;
         FftSched fy;
@@ -724,8 +735,8 @@ void tune_spec(Shape& S, cudaStream_t st) {
         if (t < tbest) { tbest = t; best.g.tile_y = tile; best.fy = fy; }
       }
     tbest = 1e30f;
-    for (int tile : batch_candidates(S.g.tile_z, S.Pz, sizeof(V)))
-      for (int order = 0; order < 3; ++order) {
+    for (int tile : batch_candidates(S.g.tile_z, S.Pz, sizeof(V), fixz))
+      for (int order = 0; order < (fixz ? 1 : 3); ++order) {
         PassGeom g = best.g;
         g.tile_z = tile;
         FftSched fz;

@@ -438,9 +438,14 @@ int x_pass_blocks(const PassGeom& g) {
   return (npairs + g.lines_x - 1) / g.lines_x;
 }
 
+// Opt a kernel in to `bytes` of dynamic shared memory.  The default limit
+// (48 KB) covers static plus dynamic shared memory, and these kernels carry up
+// to ~1.5 KB of static arrays (row offsets, reduction scratch), so the opt-in
+// starts below 48 KB of dynamic memory.
 template <typename K>
 static void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes + kStaticSmemAllowance > 48 * 1024)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <typename V>

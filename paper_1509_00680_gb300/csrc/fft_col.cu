@@ -230,7 +230,7 @@ void launch_col_len(const PassGeom& g, const V* tw, const Batch& b, const PipeAr
                     cudaStream_t st) {
   constexpr int TC = kThreads / (L / ColCfg<V, L, MODE>::E);
   const size_t sm = (size_t)(TC * line_stride<V>(L)) * sizeof(V);
-  if (sm > 48 * 1024)
+  if (sm + kStaticSmemAllowance > 48 * 1024)
     cudaFuncSetAttribute(k_col<V, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const dim3 grid((g.Hx + TC - 1) / TC, MODE == COL_Z ? g.Py : g.nz, nslots);
   count_launch();
@@ -399,10 +399,10 @@ void launch_xr_len(bool inverse, const PassGeom& g, const V* tw, const Batch& b,
   const dim3 grid((npairs + NL - 1) / NL, 1, nslots);
   count_launch();
   if (inverse) {
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_xr_inv<V, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm + kStaticSmemAllowance > 48 * 1024) cudaFuncSetAttribute(k_xr_inv<V, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_xr_inv<V, L><<<grid, kThreads, sm, st>>>(g, tw, b, a);
   } else {
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_xr_fwd<V, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm + kStaticSmemAllowance > 48 * 1024) cudaFuncSetAttribute(k_xr_fwd<V, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_xr_fwd<V, L><<<grid, kThreads, sm, st>>>(g, tw, b, a);
   }
 }

@@ -125,6 +125,11 @@ __device__ __forceinline__ size_t row_offset(const PassGeom& g, int row) {
 
 constexpr int kThreads = 256;
 
+// Upper bound on the static shared memory of a spectrum-pass kernel; a
+// launcher opts a kernel in to more dynamic shared memory once dynamic plus
+// this allowance may exceed the default 48 KB per block.
+constexpr size_t kStaticSmemAllowance = 4096;
+
 
 // Slot served by this block for a spectrum pass of precision V, or -1.
 template <typename V>
