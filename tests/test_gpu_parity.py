@@ -291,6 +291,50 @@ def test_not_converged_and_zero_source(gps, ctx):
     assert rep.iters == 0 and np.all(N(phi, p.grid.shape) == 0)
 
 
+@pytest.mark.parametrize("bc", [synth.BC_FREE, synth.BC_SURFACE, synth.BC_PERIODIC])
+def test_uniform_eps_converges_in_one_iteration(gps, ctx, bc):
+    """eps = 1 everywhere: q = 0, so A M r = -4 pi r exactly (Eq. corr) and
+    Algorithm 2 lands on the vacuum solution phi = S (rho - mean) in one
+    iteration; phi equals the oracle's vacuum solve."""
+    g = synth.Grid(24, 20, 16, 0.4, 0.45, 0.5, bc)
+    rng = np.random.default_rng(31)
+    rho = rng.standard_normal(g.shape)
+    eps = np.ones(g.shape)
+    phi = T(np.zeros(g.shape))
+    rep = ctx.gpe_solve(gps.grid_from(g), T(rho), T(eps), phi, gps.default_opts(tol_abs=1e-10))
+    assert rep.status == 0 and rep.iters == 1
+    src = rho - rho.mean() if bc == synth.BC_PERIODIC else rho
+    ref = VacuumSolver(g).apply(src)
+    assert relmax(N(phi, g.shape), ref) < 1e-12
+
+
+@pytest.mark.parametrize("dims", [(4096, 4, 4), (4, 4096, 4), (4, 4, 4096)])
+def test_maximum_transform_length(gps, ctx, dims):
+    """The longest transform the library accepts (4096 points on an axis) in
+    the shared-memory kernels, one line per CTA, in the three spectrum
+    precisions; one point more is rejected."""
+    g = synth.Grid(dims[0], dims[1], dims[2], 0.3, 0.3, 0.3, synth.BC_PERIODIC)
+    rng = np.random.default_rng(32)
+    sigma = rng.standard_normal(g.shape)
+    w = T(np.zeros(g.shape))
+    ctx.vacuum_solve(gps.grid_from(g), T(sigma), w)
+    assert relmax(N(w, g.shape), VacuumSolver(g).apply(sigma)) < 1e-12
+    eps = 1.0 + 30.0 * rng.random(g.shape)
+    r = rng.standard_normal(g.shape)
+    f = Fields(g, eps)
+    ref = f.precondition(r)
+    for code, tol in ((gps.GPS_FP64, 1e-12), (gps.GPS_DF64, 1e-12), (gps.GPS_MIXED, 2e-5)):
+        v = T(np.zeros(g.shape))
+        ctx.precondition(gps.grid_from(g), T(f.s), T(r), v, precision=code)
+        assert relmax(N(v, g.shape), ref) < tol
+    big = [d * 2 if d == 4096 else d for d in dims]
+    g2 = synth.Grid(big[0], big[1], big[2], 0.3, 0.3, 0.3, synth.BC_PERIODIC)
+    z = T(np.zeros(g2.shape))
+    with pytest.raises(gps.GpsError) as e:
+        ctx.vacuum_solve(gps.grid_from(g2), z, T(np.zeros(g2.shape)))
+    assert e.value.status == gps.GPS_ERR_INVALID
+
+
 def test_deterministic_and_host_entry_point(gps, ctx):
     p = synth.workload(2, n=32, count=5)
     g = gps.grid_from(p.grid)
