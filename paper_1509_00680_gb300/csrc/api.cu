@@ -1130,6 +1130,17 @@ int solve_direct(Pool& P, const double* rho, const double* eps, double* phi, int
   P.has_df64 = s.spec_hi == SPEC_DF64;
   put_active(P, st);
   ensure_tuned(*P.shape, P.has_mixed, P.has_df64, st);
+  // A single GPe / LPB solve runs the pipeline of its current spectrum
+  // precision only (read from the slot state after each round); a switch in
+  // mid-round leaves the rest of that round's iterations without work (the
+  // update kernels wait for their pipeline's flag), the next round runs the
+  // new precision.  Nonlinear PB re-enters the high precision at every outer
+  // step and keeps every pipeline of its pool.
+  const bool hi64 = s.spec_hi == SPEC_FP64, mixed = P.has_mixed;
+  const bool pick = mixed && !P.has_nlpb;
+  if (pick) {
+    P.has_mixed = false;   // the first round starts in the high precision
+  }
   int m = 2;
   bool first = true;
   for (;;) {
@@ -1139,6 +1150,12 @@ int solve_direct(Pool& P, const double* rho, const double* eps, double* phi, int
     ck(cudaStreamSynchronize(st));
     if (t_prof) t_prof->resolve();
     if (P.st_host[0].phase == PH_DONE || P.st_host[0].phase == PH_IDLE) break;
+    if (pick) {
+      const bool lo = P.st_host[0].spec == SPEC_FP32;
+      P.has_mixed = lo;
+      P.has_fp64 = !lo && hi64;
+      P.has_df64 = !lo && !hi64;
+    }
     if (m < 8) m *= 2;
   }
   P.slot_req[0] = nullptr;

@@ -419,7 +419,9 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
     }
   }
   if (dot_with && b.st)
-    grid_reduce(dot, b.partials + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_VR], &b.st[slot].vr);
+    if (grid_reduce(dot, b.partials + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_VR],
+                    &b.st[slot].vr) && threadIdx.x == 0)
+      b.st[slot].vdone = 1;
   if (want_wsum)
     grid_reduce(wsum, b.partials2 + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_WSUM],
                 &b.st[slot].wsum);

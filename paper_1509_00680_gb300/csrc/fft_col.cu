@@ -384,7 +384,9 @@ __global__ void __launch_bounds__(kThreads, (ColCfg<V, L, 3>::B)) k_xr_inv(PassG
       }
     }
   if (dot_with && b.st)
-    grid_reduce(dot, b.partials + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_VR], &b.st[slot].vr);
+    if (grid_reduce(dot, b.partials + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_VR],
+                    &b.st[slot].vr) && threadIdx.x == 0)
+      b.st[slot].vdone = 1;
   if (want_wsum)
     grid_reduce(wsum, b.partials2 + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_WSUM],
                 &b.st[slot].wsum);

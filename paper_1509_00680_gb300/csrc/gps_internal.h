@@ -84,6 +84,11 @@ struct SlotState {
   int use_k0, neutralize, gauge;
   int mixed, spec, spec_hi, restart, certify;   // spec: spectrum precision in use
   int newton, outer, max_outer, bad_eps;
+  // Set by the x inverse pass once v and (v, r) of this iteration exist,
+  // and by update_p once p, A p and alpha do; each update kernel acts only
+  // on its predecessor's flag (a pipeline of another precision may have
+  // been left out of the launch sequence) and clears it.
+  int vdone, pdone;
   unsigned int counter[CNT_COUNT];
 };
 

@@ -255,6 +255,8 @@ __global__ void k_init(Batch b, Fields f, size_t n) {
     S.status = GPS_OK;
     S.vr_prev = 1.0;
     S.restart = 0;
+    S.vdone = 0;
+    S.pdone = 0;
     S.spec = S.spec_hi;
     if (S.rr0 <= S.tol2) after_pcg(S);
     else S.phase = PH_ITER;
@@ -274,6 +276,7 @@ __global__ void k_init(Batch b, Fields f, size_t n) {
 // the directions (beta = 0) instead of stopping.
 __global__ void k_update_p(Batch b, Fields f, size_t n, double inv_n, int periodic) {
   SLOT_PROLOGUE(b)
+  if (!S.vdone) return;   // this iteration's preconditioner did not run for the slot
   const double* __restrict__ v = f.v + off;
   const double* __restrict__ r = f.r + off;
   const double* __restrict__ qlam = f.qlam + off;
@@ -318,6 +321,8 @@ __global__ void k_update_p(Batch b, Fields f, size_t n, double inv_n, int period
     S.vr = vr;
     S.vr_prev = vr;
     S.restart = 0;
+    S.vdone = 0;
+    S.pdone = 1;
     if (!(pap < 0.0) || !isfinite(pap) || !isfinite(vr)) {
       S.alpha = 0.0;
       if (S.spec == SPEC_FP32) {   // FP32 noise floor reached: continue in FP64 accuracy
@@ -336,6 +341,7 @@ __global__ void k_update_p(Batch b, Fields f, size_t n, double inv_n, int period
 // x += alpha p ; r -= alpha A p ; partial ||r||^2 ; convergence test.
 __global__ void k_update_r(Batch b, Fields f, size_t n) {
   SLOT_PROLOGUE(b)
+  if (!S.pdone) return;   // update_p did not run for the slot in this iteration
   const bool nl = S.kind == GPS_NLPB;
   double* __restrict__ x = (nl ? f.dphi : f.phi) + off;
   double* __restrict__ r = f.r + off;
@@ -354,6 +360,7 @@ __global__ void k_update_r(Batch b, Fields f, size_t n) {
     acc += ri * ri;
   }
   if (grid_reduce(acc, slot_partials(b, slot), &S.counter[CNT_RR], &S.rr) && threadIdx.x == 0) {
+    S.pdone = 0;
     S.iter += 1;
     S.iters_total += 1;
     if (S.spec != SPEC_FP32) S.fp64_iters += 1;
