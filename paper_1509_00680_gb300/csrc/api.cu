@@ -980,6 +980,23 @@ struct Engine {
     ensure_tuned(*P.shape, P.has_mixed, P.has_df64, P.stream);
     put_active(P, P.stream);
     const int m = 4;
+    // Pipelines of this round: the FP32 one if a slot iterates in FP32, a
+    // high-precision one if a slot is in (or, for nonlinear PB, may return
+    // to) that precision.  A slot that switches in mid-round waits for the
+    // next round (the update kernels act only after their pipeline ran).
+    const bool acc_mixed = P.has_mixed, acc_fp64 = P.has_fp64, acc_df64 = P.has_df64;
+    bool lo = false, h64 = false, hdf = false;
+    for (int k = 0; k < P.cap; ++k) {
+      if (!P.slot_req[k]) continue;
+      const SlotState& s = P.st_host[k];
+      if (s.phase == PH_DONE || s.phase == PH_IDLE) continue;
+      const bool in_lo = s.spec == SPEC_FP32;
+      lo |= in_lo;
+      if (!in_lo || s.kind == GPS_NLPB) (s.spec_hi == SPEC_FP64 ? h64 : hdf) = true;
+    }
+    P.has_mixed = acc_mixed && lo;
+    P.has_fp64 = acc_fp64 && h64;
+    P.has_df64 = acc_df64 && hdf;
     const int key = (P.has_nlpb ? 1 : 0) | (P.has_mixed ? 2 : 0) | (P.has_cert ? 4 : 0) |
                     (P.has_fp64 ? 8 : 0) | (P.has_df64 ? 16 : 0);
     const bool graphs_ok = use_graphs && !(t_prof && t_prof->on);
@@ -998,6 +1015,9 @@ struct Engine {
     } else {
       launch_round(P, m, true, true, P.stream);
     }
+    P.has_mixed = acc_mixed;
+    P.has_fp64 = acc_fp64;
+    P.has_df64 = acc_df64;
     get_states(P, P.stream);
   }
 
