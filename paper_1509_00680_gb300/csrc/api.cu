@@ -629,9 +629,17 @@ float time_launch(F&& launch, cudaStream_t st) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // warm-up launch, timed: long launches (> 1 ms, large grids) vary little
+  // between repetitions, so one more is enough; short ones take the best of 3
+  cudaEventRecord(e0, st);
   launch();
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float warm = 0.f;
+  cudaEventElapsedTime(&warm, e0, e1);
+  const int reps = warm > 1.0f ? 1 : 3;
   float best = 1e30f;
-  for (int r = 0; r < 3; ++r) {
+  for (int r = 0; r < reps; ++r) {
     cudaEventRecord(e0, st);
     launch();
     cudaEventRecord(e1, st);
