@@ -231,6 +231,7 @@ def run_ours(args, ws, rank, local):
                                                 precision=gps.GPS_DF64)
     mixed_df64 = None if args.no_mixed else run_mixed(ctx, g, rho, eps, phi, flush, args, gps,
                                                       total_ms / args.steps, precision=gps.GPS_MIXED_DF64)
+    warm = None if args.no_mixed else run_warm(gps, local, p, g, rho, eps, flush)
     serving = None if args.no_serving else run_serving(gps, local, args)
 
     # roofline of the dominant kernel (largest share of kernel time in warm-up)
@@ -254,6 +255,7 @@ def run_ours(args, ws, rank, local):
         "mixed": mixed,
         "df64": df64,
         "mixed_df64": mixed_df64,
+        "warm_start": warm,
         "serving": serving,
         "roofline": roof,
         "gpu_launches": int(launches),
@@ -298,6 +300,38 @@ def run_mixed(ctx, g, rho, eps, phi64, flush, args, gps, fp64_ms, precision=None
             "spectrum": {gps.GPS_MIXED: "fp32 after ||r|| <= 1e-2 ||r0||, fp64 before",
                          gps.GPS_DF64: "df64",
                          gps.GPS_MIXED_DF64: "fp32 after ||r|| <= 1e-2 ||r0||, df64 before"}.get(prec, prec)}
+
+
+def run_warm(gps, device, p, g, rho, eps, flush):
+    """Warm start (opts.warm_start) on the same workload: after a solve, the
+    solve for a nearby charge density (rho + 2% of itself shifted by 3 grid
+    points along z, eps unchanged) from the previous potential, against the
+    same solve from zero; FP64, ||r|| <= 1e-10."""
+    import torch
+    ctx = gps.Context(device)
+    rho2 = rho + 0.02 * torch.roll(rho.view(p.grid.shape), 3, dims=0).reshape(-1)
+    stream = torch.cuda.current_stream()
+
+    def timed(r, warm):
+        phi = torch.zeros_like(rho)
+        o = gps.default_opts(tol_abs=1e-10, warm_start=warm)
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = ctx.gpe_solve(g, r, eps, phi, o)
+        e1.record(stream)
+        e1.synchronize()
+        return phi, rep, e0.elapsed_time(e1)
+
+    timed(rho2, 0)                         # plans and tuning
+    timed(rho, 1)                          # state for the warm start
+    phi_w, rep_w, ms_w = timed(rho2, 1)
+    phi_c, rep_c, ms_c = timed(rho2, 0)
+    ctx.close()
+    return {"cold_iters": rep_c.iters, "warm_iters": rep_w.iters, "cold_ms": ms_c, "warm_ms": ms_w,
+            "warm": rep_w.warm, "rel_l2_warm_vs_cold": (torch.linalg.norm(phi_w - phi_c) /
+                                                        torch.linalg.norm(phi_c)).item(),
+            "perturbation": "rho + 0.02 * rho shifted by 3 points along z, same eps"}
 
 
 def run_serving(gps, device, args, count=None):

@@ -103,6 +103,15 @@ typedef struct {
   int precision;         /* gps_precision */
   double mixed_switch;   /* GPS_MIXED: FP64 preconditioner until ||r|| <= mixed_switch*||r_0|| */
   int certify;           /* 1: compute rep->fixed_point_res (always done for GPS_MIXED) */
+  int warm_start;        /* GPe / LPB through the single-solve entry points: 1 = when the
+                            previous solve of the same kind on this context and grid had the
+                            same eps (compared value by value on the device) and, for LPB, the
+                            same electrolyte, start from its potential, phi_0 = phi_prev, with
+                            r_0 = b - (b_prev - r_prev), b = -4 pi rho: the previous solve's
+                            final residual stands in for A phi_prev, so no operator is applied
+                            (a warm start of Algorithm 2).  Every solve with warm_start set
+                            keeps eps, phi and b - r on the device for the next one (three
+                            more grid-sized arrays in the context).  Otherwise a cold start. */
 } gps_opts;
 
 typedef struct {
@@ -119,13 +128,14 @@ typedef struct {
                              zero for the exact discrete solution (certificate of the result);
                              -1 when not computed */
   double time_ms;        /* wall time of the call (host clock, synchronized) */
+  int warm;              /* 1: the solve started from the previous one (opts.warm_start) */
 } gps_report;
 
 typedef struct gps_ctx gps_ctx;
 
 /* Fill *opts with defaults: tol_abs 1e-10, tol_rel 0, max_iter 500,
  * max_outer 100, tol_outer 1e-10, eta 0.6, Newton outer mode, forcing 1e-2,
- * FP64, mixed_switch 1e-3, certify 0. */
+ * FP64, mixed_switch 1e-2, certify 0, warm_start 0. */
 void gps_default_opts(gps_opts* opts);
 
 /* Human-readable name of a status code (static storage). */

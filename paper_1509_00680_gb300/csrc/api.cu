@@ -479,6 +479,13 @@ struct Pool {
   std::vector<Request*> slot_req;
   std::map<int, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   unsigned long long last_use = 0;
+  // warm start (single-solve pools): eps, phi and b - r of the last solve
+  // that asked for it, and the flag of the same-eps test
+  double *ws_eps = nullptr, *ws_phi = nullptr, *ws_d = nullptr;
+  int* ws_flag = nullptr;
+  bool ws_valid = false;
+  int ws_kind = -1;
+  gps_electrolyte ws_el{};
   DevMem mem;
 
   ~Pool() {
@@ -888,6 +895,7 @@ void fill_report(gps_report* rep, const SlotState& s, double t0) {
   rep->background = s.background;
   rep->fixed_point_res = s.cert;
   rep->time_ms = now_ms() - t0;
+  rep->warm = s.warm;
 }
 
 void put_state(Pool& P, int slot, const SlotState& s, cudaStream_t st) {
@@ -1150,6 +1158,33 @@ int solve_direct(Pool& P, const double* rho, const double* eps, double* phi, int
   P.f.phi = phi;
   P.slot_req[0] = reinterpret_cast<Request*>(&P);   // marks slot 0 busy
   SlotState s = initial_state(kind, el, o);
+  // warm start: same kind, same electrolyte (LPB) and eps equal value by
+  // value to the previous warm-start solve's
+  const bool keep = o.warm_start && kind != GPS_NLPB;
+  P.f.wphi = nullptr;
+  P.f.wd = nullptr;
+  if (keep) {
+    if (!P.ws_eps) {
+      P.ws_eps = P.mem.alloc<double>(P.n);
+      P.ws_phi = P.mem.alloc<double>(P.n);
+      P.ws_d = P.mem.alloc<double>(P.n);
+      P.ws_flag = P.mem.alloc<int>(1);
+    }
+    bool same = P.ws_valid && P.ws_kind == kind;
+    if (same && kind == GPS_LPB) same = el && std::memcmp(el, &P.ws_el, sizeof(gps_electrolyte)) == 0;
+    if (same) {
+      int differ = 1;
+      ck(cudaMemsetAsync(P.ws_flag, 0, sizeof(int), st));
+      launch_eps_differ(eps, P.ws_eps, P.n, P.ws_flag, st);
+      ck(cudaMemcpyAsync(&differ, P.ws_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+      ck(cudaStreamSynchronize(st));
+      if (!differ) {
+        s.warm = 1;
+        P.f.wphi = P.ws_phi;
+        P.f.wd = P.ws_d;
+      }
+    }
+  }
   put_state(P, 0, s, st);
   P.has_nlpb = kind == GPS_NLPB;
   P.has_mixed = s.mixed != 0;
@@ -1186,6 +1221,17 @@ int solve_direct(Pool& P, const double* rho, const double* eps, double* phi, int
     }
     if (m < 8) m *= 2;
   }
+  if (keep) {
+    const int stt = P.st_host[0].status;
+    P.ws_valid = stt == GPS_OK || stt == GPS_ERR_NOT_CONVERGED;
+    if (P.ws_valid) {
+      launch_warm_store(batch_of(P, PH_DONE, -1), P.f, P.ws_eps, P.ws_phi, P.ws_d, P.n, st);
+      P.ws_kind = kind;
+      if (el) P.ws_el = *el;
+    }
+  }
+  P.f.wphi = nullptr;
+  P.f.wd = nullptr;
   P.slot_req[0] = nullptr;
   P.f.rho = P.own_rho;
   P.f.eps = P.own_eps;

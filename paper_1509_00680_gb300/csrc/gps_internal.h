@@ -89,6 +89,7 @@ struct SlotState {
   // on its predecessor's flag (a pipeline of another precision may have
   // been left out of the launch sequence) and clears it.
   int vdone, pdone;
+  int warm;             // INIT starts from the previous solve (Fields wphi, wd)
   unsigned int counter[CNT_COUNT];
 };
 

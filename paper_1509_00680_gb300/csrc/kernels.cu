@@ -237,11 +237,16 @@ __global__ void k_init(Batch b, Fields f, size_t n) {
   double* p = f.p + off;
   double* Ap = f.Ap + off;
   const double bg = S.background;
+  // warm start of Algorithm 2 (x_0 = phi_prev): the previous solve's b - r
+  // stands in for A phi_prev, so r_0 = b - (b_prev - r_prev)
+  const bool warm = S.warm && f.wphi && f.wd && !nl;
+  const double* wphi = warm ? f.wphi + off : nullptr;
+  const double* wd = warm ? f.wd + off : nullptr;
   double acc = 0.0;
   GRID_STRIDE(i, n) {
-    const double ri = -kFourPi * (src[i] - bg);
+    const double ri = -kFourPi * (src[i] - bg) - (warm ? wd[i] : 0.0);
     r[i] = ri;
-    x[i] = 0.0;
+    x[i] = warm ? wphi[i] : 0.0;
     p[i] = 0.0;
     Ap[i] = 0.0;
     acc += ri * ri;
@@ -699,6 +704,38 @@ void launch_fp_residual(const Batch& b, const Fields& f, size_t n, int periodic,
                         cudaStream_t st) {
   count_launch();
   k_fp_residual<<<VEC_GRID(n, nslots)>>>(b, f, n, periodic);
+}
+
+// flag = 1 if a and b differ anywhere (the same-eps test of a warm start).
+__global__ void k_eps_differ(const double* __restrict__ a, const double* __restrict__ b, size_t n,
+                             int* flag) {
+  int d = 0;
+  GRID_STRIDE(i, n) d |= a[i] != b[i];
+  if (__syncthreads_or(d) && threadIdx.x == 0) *flag = 1;
+}
+
+void launch_eps_differ(const double* a, const double* b, size_t n, int* flag, cudaStream_t st) {
+  count_launch();
+  k_eps_differ<<<grid_blocks(n, kT), kT, 0, st>>>(a, b, n, flag);
+}
+
+// State kept for the next warm start (slot 0): eps, phi and b - r with
+// b = -4 pi (rho - background).
+__global__ void k_warm_store(Batch b, Fields f, double* __restrict__ weps, double* __restrict__ wphi,
+                             double* __restrict__ wd, size_t n) {
+  const SlotState& S = b.st[0];
+  const double bg = S.background;
+  GRID_STRIDE(i, n) {
+    weps[i] = f.eps[i];
+    wphi[i] = f.phi[i];
+    wd[i] = -kFourPi * (f.rho[i] - bg) - f.r[i];
+  }
+}
+
+void launch_warm_store(const Batch& b, const Fields& f, double* weps, double* wphi, double* wd,
+                       size_t n, cudaStream_t st) {
+  count_launch();
+  k_warm_store<<<grid_blocks(n, kT), kT, 0, st>>>(b, f, weps, wphi, wd, n);
 }
 
 // Float and double-float copies of a Green's table, made once per shape.

@@ -22,6 +22,7 @@ struct Fields {
   double *rions, *rp, *fresh, *lam, *dphi, *src;   // Algorithm 4
   double *tmp;                           // certificate source
   float *s32;                            // eps^-1/2 rounded to float (FP32 spectrum passes)
+  const double *wphi, *wd;               // warm start: previous phi and b - r (slot 0 only)
 };
 
 int vec_blocks(size_t n, int nslots);
@@ -42,6 +43,9 @@ void launch_nl_step(const Batch& b, const Fields& f, size_t n, int commit, int n
 void launch_fp_source(const Batch& b, const Fields& f, size_t n, int nslots, cudaStream_t st);
 void launch_fp_residual(const Batch& b, const Fields& f, size_t n, int periodic, int nslots,
                         cudaStream_t st);
+void launch_eps_differ(const double* a, const double* b, size_t n, int* flag, cudaStream_t st);
+void launch_warm_store(const Batch& b, const Fields& f, double* weps, double* wphi, double* wd,
+                       size_t n, cudaStream_t st);
 void launch_table_split(const double* t, float* t32, float2* tdf, size_t n, cudaStream_t st);
 void launch_ionic_charge(const double* phi, const double* eps, double* out, size_t n,
                          const IonParams& ip, cudaStream_t st);

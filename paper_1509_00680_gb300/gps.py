@@ -41,14 +41,15 @@ class gps_opts(ctypes.Structure):
                 ("tol_outer", ctypes.c_double), ("eta", ctypes.c_double),
                 ("outer_mode", ctypes.c_int), ("forcing", ctypes.c_double),
                 ("precision", ctypes.c_int), ("mixed_switch", ctypes.c_double),
-                ("certify", ctypes.c_int)]
+                ("certify", ctypes.c_int), ("warm_start", ctypes.c_int)]
 
 
 class gps_report(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
                 ("fp64_iters", ctypes.c_int), ("res0", ctypes.c_double), ("res", ctypes.c_double),
                 ("outer_res", ctypes.c_double), ("background", ctypes.c_double),
-                ("fixed_point_res", ctypes.c_double), ("time_ms", ctypes.c_double)]
+                ("fixed_point_res", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("warm", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

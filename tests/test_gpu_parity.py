@@ -335,6 +335,45 @@ def test_maximum_transform_length(gps, ctx, dims):
     assert e.value.status == gps.GPS_ERR_INVALID
 
 
+@pytest.mark.parametrize("bc,kind", [(synth.BC_FREE, "gpe"), (synth.BC_PERIODIC, "gpe"),
+                                     (synth.BC_SURFACE, "lpb")])
+def test_warm_start(gps, bc, kind):
+    """opts.warm_start: after a solve with the same eps, a solve for a nearby
+    rho starts from its potential and its final residual (reported warm),
+    needs fewer iterations than a cold start and reaches the cold solve's
+    potential (relative L2 <= 1e-10, both to ||r|| <= 1e-12 ||b||); eps
+    changed anywhere gives a cold start."""
+    rng = np.random.default_rng(41 + bc)
+    p = synth.serving_request(rng, 32, bc, kind, h=0.45)
+    g = gps.grid_from(p.grid)
+    el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+    rho1 = p.rho
+    rho2 = p.rho + 0.02 * np.roll(p.rho, 3, axis=2)
+    tol = 1e-12 * 4 * np.pi * np.linalg.norm(rho2)
+    c = gps.Context(0)
+    try:
+        def solve(rho, eps, warm):
+            phi = T(np.zeros(p.grid.shape))
+            o = gps.default_opts(tol_abs=tol, max_iter=2000, warm_start=warm)
+            rep = c.pb_solve(g, T(rho), T(eps), el, kind, phi, o)
+            assert rep.status == 0
+            return N(phi, p.grid.shape), rep
+        _, r1 = solve(rho1, p.eps, 1)
+        assert r1.warm == 0
+        phi_w, r2 = solve(rho2, p.eps, 1)
+        assert r2.warm == 1
+        phi_c, r3 = solve(rho2, p.eps, 0)
+        assert r3.warm == 0
+        assert r2.iters < r3.iters
+        assert rel2(phi_w, phi_c) <= 1e-10
+        eps3 = p.eps.copy()
+        eps3.flat[123] *= 1.0 + 1e-9
+        _, r4 = solve(rho2, eps3, 1)
+        assert r4.warm == 0
+    finally:
+        c.close()
+
+
 def test_deterministic_and_host_entry_point(gps, ctx):
     p = synth.workload(2, n=32, count=5)
     g = gps.grid_from(p.grid)
