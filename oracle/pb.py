@@ -2,7 +2,8 @@
 
 Test infrastructure only (see the package docstring).
 
-Ionic charge (Eqs. rhoions, ionsconcPB), atomic units:
+Ionic charge (Eqs. rhoions, ionsconcPB; with ion radii and a packing
+coefficient the steric Eq. ionsconcMPB, see ion_concentrations), atomic units:
     rho_ions[phi] = gamma(r) sum_i Z_i n_i exp(-Z_i phi / kT),
 with n_i the bulk number densities and gamma the ion-exclusion function, here
 the cavity function gamma = (eps - 1)/(eps0 - 1) (so ions live only in the
@@ -26,7 +27,7 @@ algorithm remains available as mode="printed".
 """
 import numpy as np
 
-from .constants import EXP_CAP, kT, lambda0, number_density
+from .constants import EXP_CAP, kT, lambda0, max_number_density, number_density
 from .operators import Fields
 from .pcg import pcg
 
@@ -35,22 +36,54 @@ def exclusion_from_eps(eps, eps0):
     return (eps - 1.0) / (eps0 - 1.0)
 
 
-def ionic_charge(phi, gamma, electrolyte):
+def steric_ratios(electrolyte):
+    """a_j = c_j^inf / c_j^max of Eq. (ionsconcMPB), or None for the plain
+    Boltzmann distribution of Eq. (ionsconcPB) (no packing coefficient)."""
+    packing = getattr(electrolyte, "packing", 0.0) or 0.0
+    radii = getattr(electrolyte, "radius_angstrom", None)
+    if packing <= 0.0 or radii is None:
+        return None
+    return [number_density(c) / max_number_density(r, packing)
+            for c, r in zip(electrolyte.c_molar, radii)]
+
+
+def ion_concentrations(phi, electrolyte):
+    """Number densities n_i[phi] of Eq. (ionsconcPB), or of Eq. (ionsconcMPB)
+    when the electrolyte has ion radii and a packing coefficient:
+        n_i = n_i^inf e_i / (1 + sum_j a_j (e_j - 1)),  e_i = exp(-Z_i phi / kT).
+    Reading: the paper prints the bracket as (e_j + 1); with "+ 1" the bulk
+    concentration is not recovered where phi = 0, so it is read as the
+    Bikerman form "- 1" (both forms give Eq. (ionsconcPB) as c_max -> inf)."""
     kt = kT(electrolyte.temperature)
-    out = np.zeros_like(phi)
-    for z, c in zip(electrolyte.z, electrolyte.c_molar):
-        out += z * number_density(c) * np.exp(np.minimum(-z * phi / kt, EXP_CAP))
-    return gamma * out
+    e = [np.exp(np.minimum(-z * phi / kt, EXP_CAP)) for z in electrolyte.z]
+    a = steric_ratios(electrolyte)
+    den = 1.0
+    if a is not None:
+        den = 1.0 + sum(aj * (ej - 1.0) for aj, ej in zip(a, e))
+    return [number_density(c) * ei / den for c, ei in zip(electrolyte.c_molar, e)]
+
+
+def ionic_charge(phi, gamma, electrolyte):
+    """rho_ions[phi] = gamma sum_i Z_i n_i[phi] (Eq. rhoions)."""
+    n = ion_concentrations(phi, electrolyte)
+    return gamma * sum(z * ni for z, ni in zip(electrolyte.z, n))
 
 
 def ionic_charge_derivative(phi, gamma, electrolyte):
-    """d rho_ions / d phi (zero where the exponent cap is active)."""
+    """d rho_ions / d phi (a species' exponential counts as constant where
+    its cap is active)."""
     kt = kT(electrolyte.temperature)
-    out = np.zeros_like(phi)
-    for z, c in zip(electrolyte.z, electrolyte.c_molar):
-        u = -z * phi / kt
-        out += np.where(u < EXP_CAP, -z * z * number_density(c) / kt * np.exp(np.minimum(u, EXP_CAP)), 0.0)
-    return gamma * out
+    us = [-z * phi / kt for z in electrolyte.z]
+    e = [np.exp(np.minimum(u, EXP_CAP)) for u in us]
+    de = [np.where(u < EXP_CAP, -z / kt * ei, 0.0) for u, z, ei in zip(us, electrolyte.z, e)]
+    num = sum(z * number_density(c) * ei for z, c, ei in zip(electrolyte.z, electrolyte.c_molar, e))
+    dnum = sum(z * number_density(c) * dei for z, c, dei in zip(electrolyte.z, electrolyte.c_molar, de))
+    a = steric_ratios(electrolyte)
+    if a is None:
+        return gamma * dnum
+    den = 1.0 + sum(aj * (ej - 1.0) for aj, ej in zip(a, e))
+    dden = sum(aj * dej for aj, dej in zip(a, de))
+    return gamma * (dnum * den - num * dden) / (den * den)
 
 
 def linear_lambda(gamma, electrolyte):

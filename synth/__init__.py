@@ -67,10 +67,14 @@ class Grid:
 
 @dataclass
 class Electrolyte:
-    """Mobile ion species: valences z_i and bulk concentrations c_i (mol/L)."""
+    """Mobile ion species: valences z_i and bulk concentrations c_i (mol/L);
+    with effective radii R_i (angstrom) and a packing coefficient p > 0 the
+    steric (modified PB) distribution applies."""
     z: tuple = (1, -1)
     c_molar: tuple = (0.1, 0.1)
     temperature: float = 300.0
+    radius_angstrom: tuple = None
+    packing: float = 0.0
 
 
 @dataclass

@@ -362,6 +362,74 @@ def test_nlpb_reduces_to_gpe_and_lpb():
     assert np.linalg.norm(phi_nl - phi_l) <= 1e-5 * np.linalg.norm(phi_l)
 
 
+# ------------------------------------------------------------- modified PB --
+
+# The paper's steric test electrolyte: monovalent, p = 0.74, R = 3 angstrom,
+# 100 mol/m^3 = 0.1 mol/L, 300 K.
+E3 = synth.Electrolyte((1, -1), (0.1, 0.1), 300.0, radius_angstrom=(3.0, 3.0), packing=0.74)
+R3_BOHR = 3.0e-10 / 5.29177210903e-11
+NMAX_E3 = 0.74 / (4.0 / 3.0 * math.pi * R3_BOHR ** 3)    # Eq. (maxconc), bohr^-3
+
+
+def test_mpb_bulk_and_pb_limit():
+    """Eq. (ionsconcMPB): the bulk concentration where phi = 0, and the
+    Boltzmann form of Eq. (ionsconcPB) when c_max -> infinity (R -> 0)."""
+    n0 = pb.ion_concentrations(np.zeros(3), E3)
+    n_bulk = 0.1 * 1000 * 6.02214076e23 * 5.29177210903e-11 ** 3
+    for ni in n0:
+        assert np.all(ni == n_bulk)
+    phi = np.linspace(-0.02, 0.02, 81)
+    tiny = synth.Electrolyte((1, -1), (0.1, 0.1), 300.0, radius_angstrom=(1e-5, 1e-5), packing=0.74)
+    plain = synth.Electrolyte((1, -1), (0.1, 0.1), 300.0)
+    gam = np.full_like(phi, 0.7)
+    a, b = pb.ionic_charge(phi, gam, tiny), pb.ionic_charge(phi, gam, plain)
+    assert np.allclose(a, b, rtol=1e-9, atol=0)
+    da, db = pb.ionic_charge_derivative(phi, gam, tiny), pb.ionic_charge_derivative(phi, gam, plain)
+    assert np.allclose(da, db, rtol=1e-9, atol=0)
+
+
+def test_mpb_saturates_at_cmax_as_the_paper_reports():
+    """No concentration exceeds c_max of Eq. (maxconc), and with the paper's
+    parameters the ionic density saturates once |phi| exceeds ~0.01 a.u.
+    (the inset of the modified-PB convergence figure), where the Boltzmann
+    distribution would be ~300 times denser."""
+    phi = np.linspace(-0.2, 0.2, 4001)
+    for ni in pb.ion_concentrations(phi, E3):
+        assert ni.max() <= NMAX_E3 * (1 + 1e-12)
+    one = np.ones(1)
+    for v in (0.01, -0.01):
+        rho = abs(pb.ionic_charge(np.array([v]), one, E3)[0])
+        assert 0.97 * NMAX_E3 <= rho <= NMAX_E3
+        plain = abs(pb.ionic_charge(np.array([v]), one, synth.Electrolyte((1, -1), (0.1, 0.1), 300.0))[0])
+        assert plain > 300 * NMAX_E3
+    assert abs(pb.ionic_charge(np.array([0.001]), one, E3)[0]) < 0.1 * NMAX_E3
+
+
+def test_mpb_derivative_matches_finite_differences():
+    phi = np.linspace(-0.03, 0.03, 61)
+    gam = np.full_like(phi, 0.9)
+    h = 1e-7
+    fd = (pb.ionic_charge(phi + h, gam, E3) - pb.ionic_charge(phi - h, gam, E3)) / (2 * h)
+    d = pb.ionic_charge_derivative(phi, gam, E3)
+    assert np.allclose(d, fd, rtol=1e-5, atol=1e-9 * np.abs(d).max())
+
+
+def test_mpb_alg4_matches_dense_newton():
+    """Algorithm 4 (Newton) with the steric charge against a dense Newton
+    solve, on a box where the potential enters the saturated regime."""
+    g, rho, eps, _, e0 = _nl_problem()
+    rho = rho * 40.0
+    el = synth.Electrolyte((1, -1), (0.5, 0.5), 300.0, radius_angstrom=(3.0, 3.0), packing=0.74)
+    phi, info = oracle.solve_nlpb(g, rho, eps, el, e0, tol=1e-12, max_outer=300)
+    assert info["converged"]
+    gam = pb.exclusion_from_eps(eps, e0)
+    ref, _ = dense.newton_nlpb(Fields(g, eps), rho, gam, el)
+    assert np.linalg.norm(phi - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert np.abs(ref).max() > 0.01          # reaches the saturated regime
+    sat = np.abs(pb.ionic_charge(ref, gam, el)) / gam.clip(1e-30)
+    assert sat.max() > 0.9 * 0.74 / (4.0 / 3.0 * math.pi * R3_BOHR ** 3)
+
+
 def test_electrolyte_units():
     """Debye length of a 1:1 electrolyte at 0.1 M in water at 300 K is about
     0.96 nm = 18.2 bohr; lambda0/eps0 = kappa^2."""
