@@ -232,6 +232,7 @@ def run_ours(args, ws, rank, local):
     mixed_df64 = None if args.no_mixed else run_mixed(ctx, g, rho, eps, phi, flush, args, gps,
                                                       total_ms / args.steps, precision=gps.GPS_MIXED_DF64)
     warm = None if args.no_mixed else run_warm(gps, local, p, g, rho, eps, flush)
+    nonlinear = None if args.no_nonlinear else run_nonlinear(gps, local, flush)
     serving = None if args.no_serving else run_serving(gps, local, args)
 
     # roofline of the dominant kernel (largest share of kernel time in warm-up)
@@ -256,6 +257,7 @@ def run_ours(args, ws, rank, local):
         "df64": df64,
         "mixed_df64": mixed_df64,
         "warm_start": warm,
+        "nonlinear": nonlinear,
         "serving": serving,
         "roofline": roof,
         "gpu_launches": int(launches),
@@ -332,6 +334,46 @@ def run_warm(gps, device, p, g, rho, eps, flush):
             "warm": rep_w.warm, "rel_l2_warm_vs_cold": (torch.linalg.norm(phi_w - phi_c) /
                                                         torch.linalg.norm(phi_c)).item(),
             "perturbation": "rho + 0.02 * rho shifted by 3 points along z, same eps"}
+
+
+def run_nonlinear(gps, device, flush):
+    """Nonlinear PB on the free-BC 256^3 union-of-spheres workload (200
+    Gaussians, 1:1 electrolyte at 0.5 M, 300 K): Eq. (PBe) with the Boltzmann
+    ionic charge, and the modified (steric) PB with p = 0.74 and R = 3
+    angstrom for both species, each by the Newton outer loop around
+    Algorithm 2 on the mixed-precision path (double-float spectrum, FP32 once
+    ||r|| <= 1e-2 ||r0||, FP64 certificate), outer tolerance 1e-10.  One
+    untimed solve per problem first (plans, tuning)."""
+    import torch
+    import synth
+    p = synth.workload(4)
+    g = gps.grid_from(p.grid)
+    rho = torch.from_numpy(p.rho.ravel()).to(device)
+    eps = torch.from_numpy(p.eps.ravel()).to(device)
+    e = p.electrolyte
+    els = {"nlpb": ("nlpb", gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0)),
+           "mpb": ("mpb", gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0,
+                                               radius_angstrom=(3.0,) * len(e.z), packing=0.74))}
+    ctx = gps.Context(device)
+    stream = torch.cuda.current_stream()
+    opts = gps.default_opts(tol_outer=1e-10, max_iter=3000, precision=gps.GPS_MIXED_DF64)
+    out = {"workload": p.name, "grid": list(p.grid.shape), "precision": "mixed_df64",
+           "steric": {"packing": 0.74, "radius_angstrom": 3.0}}
+    for name, (kind, el) in els.items():
+        phi = torch.zeros_like(rho)
+        ctx.pb_solve(g, rho, eps, el, kind, phi, opts)
+        phi.zero_()
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = ctx.pb_solve(g, rho, eps, el, kind, phi, opts)
+        e1.record(stream)
+        e1.synchronize()
+        out[name] = {"ms": e0.elapsed_time(e1), "status": rep.status, "outer_iters": rep.outer_iters,
+                     "pcg_iters": rep.iters, "fp64_iters": rep.fp64_iters,
+                     "outer_res": rep.outer_res, "fixed_point_res": rep.fixed_point_res}
+    ctx.close()
+    return out
 
 
 def run_serving(gps, device, args, count=None):
@@ -606,6 +648,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-nonlinear", action="store_true")
     ap.add_argument("--clocks-log", default=None, help="keep the nvidia-smi samples of the timed region here")
     ap.add_argument("--serving-count", type=int, default=24)
     ap.add_argument("--passes", default=None, choices=sorted(PASS_CASES),

@@ -59,7 +59,7 @@ typedef enum {
  *                   FP32 pipe, which on GB300 issues 64x the FP64 rate.
  *   GPS_MIXED_DF64  double-float spectrum until the switch, then FP32. */
 typedef enum { GPS_FP64 = 0, GPS_MIXED = 1, GPS_DF64 = 2, GPS_MIXED_DF64 = 3 } gps_precision;
-typedef enum { GPS_GPE = 0, GPS_LPB = 1, GPS_NLPB = 2 } gps_problem;
+typedef enum { GPS_GPE = 0, GPS_LPB = 1, GPS_NLPB = 2, GPS_MPB = 3 } gps_problem;
 typedef enum { GPS_OUTER_NEWTON = 0, GPS_OUTER_PRINTED = 1 } gps_outer_mode;
 
 /* Uniform orthorhombic grid.  nx, ny, nz >= 4; each padded FFT length
@@ -84,6 +84,15 @@ typedef struct {
   double c_molar[GPS_MAX_SPECIES];
   double temperature;    /* K */
   double eps0;           /* bulk dielectric constant of the solvent (for gamma) */
+  /* Steric (modified PB, GPS_MPB) parameters, Eqs. (ionsconcMPB, maxconc):
+   * effective ion radii R_i and packing coefficient p give the maximum
+   * concentration c_i^max = p / ((4/3) pi R_i^3 N_A) and
+   * c_i = c_i^inf e_i / (1 + sum_j (c_j^inf / c_j^max)(e_j - 1)),
+   * e_i = exp(-Z_i phi / kT) (the paper prints "+ 1" in the bracket; read as
+   * "- 1", the form that gives c_i^inf where phi = 0).  Unused (zero) for the
+   * other problems. */
+  double radius_angstrom[GPS_MAX_SPECIES];
+  double packing;
 } gps_electrolyte;
 
 /* Solver options.  Convergence of Algorithm 2 is tested on the Euclidean norm
@@ -165,7 +174,10 @@ int gps_gpe_solve(gps_ctx* ctx, const gps_grid* grid, const double* rho_dev,
  * kind = GPS_NLPB: nonlinear PB, Eqs. (PBe, rhoions, ionsconcPB), by the
  * outer loop of Algorithm 4 (opts->outer_mode selects the printed linear
  * mixing or the Newton-linearized inner operator), each inner solve by
- * Algorithm 2.  kind = GPS_GPE ignores the electrolyte. */
+ * Algorithm 2.  kind = GPS_MPB: modified (steric) PB, Eqs. (PBe, rhoions,
+ * ionsconcMPB, maxconc), by the same outer loop; needs packing > 0 and
+ * radius_angstrom > 0 for every species (else GPS_ERR_INVALID).
+ * kind = GPS_GPE ignores the electrolyte. */
 int gps_pb_solve(gps_ctx* ctx, const gps_grid* grid, const double* rho_dev,
                  const double* eps_dev, const gps_electrolyte* el, int kind,
                  double* phi_dev, const gps_opts* opts, gps_report* rep,

@@ -124,7 +124,7 @@ std::vector<double> cosine_matrix(int M, int K, double scale) {
   return C;
 }
 
-IonParams ion_params(const gps_electrolyte* el) {
+IonParams ion_params(const gps_electrolyte* el, bool steric = false) {
   const double NA = 6.02214076e23, a0 = 5.29177210903e-11, kB = 3.1668115634556e-6;
   IonParams ip;
   std::memset(&ip, 0, sizeof(ip));
@@ -144,7 +144,24 @@ IonParams ion_params(const gps_electrolyte* el) {
     l += ip.z2n_kt[s];
   }
   ip.lambda0 = kFourPi * l;
+  if (steric) {
+    // Eq. (maxconc) as a number density: p / ((4/3) pi R^3), R in bohr
+    ip.steric = 1;
+    for (int s = 0; s < el->nspecies; ++s) {
+      const double r = el->radius_angstrom[s] * 1e-10 / a0;
+      const double nmax = el->packing / (4.0 / 3.0 * kPi * r * r * r);
+      ip.a[s] = el->c_molar[s] * 1000.0 * NA * a0 * a0 * a0 / nmax;
+    }
+  }
   return ip;
+}
+
+// Modified PB needs a packing coefficient and a radius per species.
+int validate_steric(const gps_electrolyte* el) {
+  if (!el || !(el->packing > 0)) return GPS_ERR_INVALID;
+  for (int s = 0; s < el->nspecies; ++s)
+    if (!(el->radius_angstrom[s] > 0)) return GPS_ERR_INVALID;
+  return GPS_OK;
 }
 
 int validate_grid(const gps_grid* g) {
@@ -855,10 +872,13 @@ void launch_round(Pool& P, int m, bool setup, bool init, cudaStream_t st) {
 }
 
 // The slot state of a new request.
+// kind GPS_MPB runs as GPS_NLPB with the steric ionic charge.
 SlotState initial_state(int kind, const gps_electrolyte* el, const gps_opts& o) {
   SlotState s;
   std::memset(&s, 0, sizeof(s));
-  s.ion = ion_params(kind == GPS_GPE ? nullptr : el);
+  const bool steric = kind == GPS_MPB;
+  if (steric) kind = GPS_NLPB;
+  s.ion = ion_params(kind == GPS_GPE ? nullptr : el, steric);
   s.phase = PH_SETUP;
   s.kind = kind;
   s.status = GPS_OK;
@@ -985,7 +1005,7 @@ struct Engine {
     ck(cudaMemcpyAsync(P.f.eps + k * P.n, q.eps_host, b, cudaMemcpyHostToDevice, P.stream));
     SlotState s = initial_state(q.kind, &q.el, q.opts);
     put_state(P, k, s, P.stream);
-    P.has_nlpb |= q.kind == GPS_NLPB;
+    P.has_nlpb |= q.kind == GPS_NLPB || q.kind == GPS_MPB;
     P.has_mixed |= s.mixed != 0;
     P.has_cert |= s.certify != 0;
     P.has_fp64 |= s.spec_hi == SPEC_FP64;
@@ -1067,7 +1087,8 @@ struct Engine {
       Request* r = *it;
       int v = validate_grid(&r->req.grid);
       if (v == GPS_OK && r->req.kind != GPS_GPE) v = validate_el(&r->req.el);
-      if (v == GPS_OK && (r->req.kind < GPS_GPE || r->req.kind > GPS_NLPB)) v = GPS_ERR_INVALID;
+      if (v == GPS_OK && (r->req.kind < GPS_GPE || r->req.kind > GPS_MPB)) v = GPS_ERR_INVALID;
+      if (v == GPS_OK && r->req.kind == GPS_MPB) v = validate_steric(&r->req.el);
       if (v == GPS_OK && (!r->req.rho_host || !r->req.eps_host || !r->req.phi_host)) v = GPS_ERR_INVALID;
       if (v != GPS_OK) {
         r->status = v;
@@ -1160,7 +1181,7 @@ int solve_direct(Pool& P, const double* rho, const double* eps, double* phi, int
   SlotState s = initial_state(kind, el, o);
   // warm start: same kind, same electrolyte (LPB) and eps equal value by
   // value to the previous warm-start solve's
-  const bool keep = o.warm_start && kind != GPS_NLPB;
+  const bool keep = o.warm_start && kind != GPS_NLPB && kind != GPS_MPB;
   P.f.wphi = nullptr;
   P.f.wd = nullptr;
   if (keep) {
@@ -1186,7 +1207,7 @@ int solve_direct(Pool& P, const double* rho, const double* eps, double* phi, int
     }
   }
   put_state(P, 0, s, st);
-  P.has_nlpb = kind == GPS_NLPB;
+  P.has_nlpb = kind == GPS_NLPB || kind == GPS_MPB;
   P.has_mixed = s.mixed != 0;
   P.has_cert = s.certify != 0;
   P.has_fp64 = s.spec_hi == SPEC_FP64;
@@ -1419,7 +1440,8 @@ int gps_pb_solve(gps_ctx* ctx, const gps_grid* grid, const double* rho, const do
   const double t0 = now_ms();
   if (rep) std::memset(rep, 0, sizeof(*rep));
   if (!ctx || !rho || !eps || !phi) return GPS_ERR_INVALID;
-  if (kind < GPS_GPE || kind > GPS_NLPB) return GPS_ERR_INVALID;
+  if (kind < GPS_GPE || kind > GPS_MPB) return GPS_ERR_INVALID;
+  if (kind == GPS_MPB && validate_steric(el) != GPS_OK) return GPS_ERR_INVALID;
   int v = validate_grid(grid);
   if (v != GPS_OK) return v;
   if (kind != GPS_GPE && (v = validate_el(el)) != GPS_OK) return v;
@@ -1448,7 +1470,8 @@ int gps_pb_solve_host(gps_ctx* ctx, const gps_grid* grid, const double* rho_h, c
   const double t0 = now_ms();
   if (rep) std::memset(rep, 0, sizeof(*rep));
   if (!ctx || !rho_h || !eps_h || !phi_h) return GPS_ERR_INVALID;
-  if (kind < GPS_GPE || kind > GPS_NLPB) return GPS_ERR_INVALID;
+  if (kind < GPS_GPE || kind > GPS_MPB) return GPS_ERR_INVALID;
+  if (kind == GPS_MPB && validate_steric(el) != GPS_OK) return GPS_ERR_INVALID;
   int v = validate_grid(grid);
   if (v != GPS_OK) return v;
   if (kind != GPS_GPE && (v = validate_el(el)) != GPS_OK) return v;
@@ -1566,7 +1589,9 @@ int gps_ionic_charge(gps_ctx* ctx, const gps_grid* grid, const double* phi, cons
   GPS_GUARD_BEGIN
   cudaSetDevice(ctx->device);
   const size_t n = (size_t)grid->nx * grid->ny * grid->nz;
-  launch_ionic_charge(phi, eps, out, n, ion_params(el), st);
+  const bool steric = el->packing > 0;
+  if (steric && validate_steric(el) != GPS_OK) return GPS_ERR_INVALID;
+  launch_ionic_charge(phi, eps, out, n, ion_params(el, steric), st);
   return finish(GPS_OK, st);
   GPS_GUARD_END
 }

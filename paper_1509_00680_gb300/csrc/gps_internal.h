@@ -59,6 +59,8 @@ struct IonParams {
   double inv_eps0m1;               // 1/(eps0 - 1)
   double exp_cap;
   double lambda0;                  // 4 pi sum z_i^2 n_i / kT
+  int steric;                      // modified PB (Eq. ionsconcMPB)
+  double a[GPS_MAX_SPECIES];       // n_i^inf / n_i^max (Eq. maxconc)
 };
 
 // Device state of one slot (one request).

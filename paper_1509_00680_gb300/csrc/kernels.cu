@@ -146,15 +146,27 @@ __global__ void k_fd16_q(Batch b, Fields f, int nx, int ny, int nz, double ihx2,
   }
 }
 
+// Ionic charge gamma sum_i Z_i n_i[phi] and its derivative in phi (Eqs.
+// rhoions, ionsconcPB; with ip.steric the Bikerman denominator of Eq.
+// ionsconcMPB, 1 + sum_j a_j (e_j - 1), a_j = n_j^inf / n_j^max).  A
+// species' exponential counts as constant where its cap is active.
 __device__ __forceinline__ void ion_terms(double phi, double gamma, const IonParams& ip,
                                           double* rho_i, double* drho) {
-  double a = 0.0, d = 0.0;
+  double a = 0.0, d = 0.0, den = 1.0, dden = 0.0;
   for (int s = 0; s < ip.nspecies; ++s) {
     const double u = -ip.zq[s] * phi * ip.inv_kt;
     const double capped = fmin(u, ip.exp_cap);
     const double e = exp(capped);
     a += ip.zn[s] * e;
     if (u < ip.exp_cap) d -= ip.z2n_kt[s] * e;
+    if (ip.steric) {
+      den += ip.a[s] * (e - 1.0);
+      if (u < ip.exp_cap) dden -= ip.a[s] * ip.zq[s] * ip.inv_kt * e;
+    }
+  }
+  if (ip.steric) {
+    d = (d * den - a * dden) / (den * den);
+    a /= den;
   }
   *rho_i = gamma * a;
   *drho = gamma * d;

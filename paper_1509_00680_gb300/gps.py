@@ -17,10 +17,10 @@ GPS_OK, GPS_ERR_INVALID, GPS_ERR_NOMEM, GPS_ERR_NOT_CONVERGED = 0, 1, 2, 3
 GPS_ERR_BREAKDOWN, GPS_ERR_TIMEOUT, GPS_ERR_CUDA, GPS_PENDING = 4, 5, 6, 7
 GPS_BC_FREE, GPS_BC_PERIODIC, GPS_BC_SURFACE = 0, 1, 2
 GPS_FP64, GPS_MIXED, GPS_DF64, GPS_MIXED_DF64 = 0, 1, 2, 3
-GPS_GPE, GPS_LPB, GPS_NLPB = 0, 1, 2
+GPS_GPE, GPS_LPB, GPS_NLPB, GPS_MPB = 0, 1, 2, 3
 GPS_OUTER_NEWTON, GPS_OUTER_PRINTED = 0, 1
 GPS_MAX_SPECIES = 8
-KIND = {"gpe": GPS_GPE, "lpb": GPS_LPB, "nlpb": GPS_NLPB}
+KIND = {"gpe": GPS_GPE, "lpb": GPS_LPB, "nlpb": GPS_NLPB, "mpb": GPS_MPB}
 
 
 class gps_grid(ctypes.Structure):
@@ -32,7 +32,8 @@ class gps_grid(ctypes.Structure):
 class gps_electrolyte(ctypes.Structure):
     _fields_ = [("nspecies", ctypes.c_int), ("z", ctypes.c_int * GPS_MAX_SPECIES),
                 ("c_molar", ctypes.c_double * GPS_MAX_SPECIES),
-                ("temperature", ctypes.c_double), ("eps0", ctypes.c_double)]
+                ("temperature", ctypes.c_double), ("eps0", ctypes.c_double),
+                ("radius_angstrom", ctypes.c_double * GPS_MAX_SPECIES), ("packing", ctypes.c_double)]
 
 
 class gps_opts(ctypes.Structure):
@@ -140,14 +141,19 @@ def grid_from(g):
     return make_grid(g.nx, g.ny, g.nz, g.hx, g.hy, g.hz, g.bc)
 
 
-def make_electrolyte(z, c_molar, temperature=300.0, eps0=78.36):
+def make_electrolyte(z, c_molar, temperature=300.0, eps0=78.36, radius_angstrom=None, packing=0.0):
+    """Electrolyte description; radius_angstrom (per species) and packing > 0
+    select the steric distribution of the modified PB problem ("mpb")."""
     el = gps_electrolyte()
     el.nspecies = len(z)
     for i, (zi, ci) in enumerate(zip(z, c_molar)):
         el.z[i] = int(zi)
         el.c_molar[i] = float(ci)
+        if radius_angstrom is not None:
+            el.radius_angstrom[i] = float(radius_angstrom[i])
     el.temperature = float(temperature)
     el.eps0 = float(eps0)
+    el.packing = float(packing)
     return el
 
 

@@ -160,6 +160,12 @@ def test_precondition_column_kernels(gps, ctx, bc, n, h, prec, tol):
     assert relmax(N(v, g.shape), f.precondition(r)) < tol
 
 
+def _has_solvent(p):
+    """A slab test box must reach above the interface (z = 10 bohr): below it
+    eps = 1 and the problem is vacuum Poisson."""
+    return oracle.pb.exclusion_from_eps(p.eps, p.eps0).max() > 0.99
+
+
 def _solve_pair(gps, ctx, p, kind="gpe", tol_rel=1e-13, **okw):
     g = p.grid
     phi = T(np.zeros(g.shape))
@@ -203,15 +209,17 @@ def test_gpe_periodic_cluster_small(gps, ctx):
 
 
 def test_gpe_surface_small(gps, ctx):
-    p = synth.workload(3, nxy=40, nz=64, count=8)
+    p = synth.workload(3, nxy=40, nz=96, count=8)
+    assert _has_solvent(p)
     got, ref, rep, info = _solve_pair(gps, ctx, p)
     assert rel2(got, ref) <= 1e-10
 
 
 @pytest.mark.parametrize("wl,kw", [(1, dict(n=40)), (2, dict(n=36, count=6)),
-                                   (3, dict(nxy=32, nz=48, count=6))])
+                                   (3, dict(nxy=32, nz=96, count=6))])
 def test_lpb(gps, ctx, wl, kw):
     p = synth.workload(wl, **kw)
+    assert _has_solvent(p)
     if p.electrolyte is None:
         p.electrolyte = synth.Electrolyte((1, -1), (0.3, 0.3), 300.0)
     got, ref, rep, info = _solve_pair(gps, ctx, p, kind="lpb")
@@ -220,7 +228,10 @@ def test_lpb(gps, ctx, wl, kw):
 
 
 def test_nlpb_newton_surface_small(gps, ctx):
-    p = synth.workload(3, nxy=32, nz=64, count=8, kind="nlpb")
+    # nz = 96 puts the top of the box (z = 16.8 bohr) above the interface at
+    # z = 10, so part of the grid is solvent and carries ionic charge.
+    p = synth.workload(3, nxy=32, nz=96, count=8, kind="nlpb")
+    assert _has_solvent(p)
     el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
     phi = T(np.zeros(p.grid.shape))
     opts = gps.default_opts(tol_outer=1e-11, max_iter=3000)
@@ -260,6 +271,93 @@ def test_ionic_charge(gps, ctx):
     ctx.ionic_charge(gps.grid_from(g), T(phi), T(eps), el, out)
     ref = oracle.pb.ionic_charge(phi, oracle.pb.exclusion_from_eps(eps, synth.EPS_WATER), el_o)
     assert relmax(N(out, g.shape), ref) < 1e-13
+
+
+# ------------------------------------------------------------ modified PB --
+
+def _steric(el, radius=3.0, packing=0.74):
+    """The paper's steric parameters (p = 0.74, R = 3 angstrom) on an electrolyte."""
+    return synth.Electrolyte(el.z, el.c_molar, el.temperature, radius_angstrom=(radius,) * len(el.z),
+                             packing=packing)
+
+
+def _gps_el(gps, el, eps0):
+    return gps.make_electrolyte(el.z, el.c_molar, el.temperature, eps0,
+                                radius_angstrom=el.radius_angstrom, packing=el.packing)
+
+
+@pytest.mark.parametrize("wl,kw,scale", [
+    (3, dict(nxy=32, nz=96, count=8, kind="nlpb"), 1.0),
+    (4, dict(n=48, count=6, margin=5.0, kind="nlpb", conc=0.5), 1.0),
+])
+def test_mpb_against_oracle(gps, ctx, wl, kw, scale):
+    """Modified PB (Eq. ionsconcMPB) by the Newton outer loop, FP64, against
+    the oracle; the steric term changes the potential (it is not plain PB)."""
+    p = synth.workload(wl, **kw)
+    el_o = _steric(p.electrolyte)
+    el = _gps_el(gps, el_o, p.eps0)
+    rho = p.rho * scale
+    phi = T(np.zeros(p.grid.shape))
+    opts = gps.default_opts(tol_outer=1e-11, max_iter=3000)
+    rep = ctx.pb_solve(gps.grid_from(p.grid), T(rho), T(p.eps), el, "mpb", phi, opts)
+    ref, info = oracle.solve_nlpb(p.grid, rho, p.eps, el_o, p.eps0, tol=1e-11, max_iter=3000)
+    assert info["converged"] and rep.status == 0
+    if p.grid.bc == synth.BC_FREE:
+        assert rep.outer_iters <= 8          # the paper reports about five (free BC)
+    got = N(phi, p.grid.shape)
+    assert rel2(got, ref) <= 1e-9
+    plain, _ = oracle.solve_nlpb(p.grid, rho, p.eps, p.electrolyte, p.eps0, tol=1e-11, max_iter=3000)
+    assert rel2(got, plain) > 1e-6
+
+
+def test_mpb_mixed_df64(gps, ctx):
+    p = synth.workload(4, n=48, count=6, margin=5.0, kind="nlpb", conc=0.5)
+    el_o = _steric(p.electrolyte)
+    phi = T(np.zeros(p.grid.shape))
+    opts = gps.default_opts(tol_outer=1e-10, max_iter=3000, precision=gps.GPS_MIXED_DF64)
+    rep = ctx.pb_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), _gps_el(gps, el_o, p.eps0), "mpb", phi, opts)
+    ref, info = oracle.solve_nlpb(p.grid, p.rho, p.eps, el_o, p.eps0, tol=1e-11, max_iter=3000)
+    assert rep.status == 0 and info["converged"]
+    assert 0 <= rep.fixed_point_res < 1e-8
+    assert rel2(N(phi, p.grid.shape), ref) <= 1e-8
+
+
+def test_ionic_charge_steric(gps, ctx):
+    g = synth.Grid(10, 12, 14, 0.5, 0.5, 0.5, synth.BC_FREE)
+    rng = np.random.default_rng(16)
+    phi = 0.03 * rng.standard_normal(g.shape)
+    phi[0, 0, :3] = [1.0, -1.0, 0.5]      # exponent cap active
+    eps = 1.0 + 77.36 * rng.random(g.shape)
+    el_o = synth.Electrolyte((1, -1, 2), (0.1, 0.1, 0.05), 310.0, radius_angstrom=(3.0, 2.5, 3.5),
+                             packing=0.74)
+    out = T(np.zeros(g.shape))
+    ctx.ionic_charge(gps.grid_from(g), T(phi), T(eps), _gps_el(gps, el_o, synth.EPS_WATER), out)
+    ref = oracle.pb.ionic_charge(phi, oracle.pb.exclusion_from_eps(eps, synth.EPS_WATER), el_o)
+    assert relmax(N(out, g.shape), ref) < 1e-13
+
+
+def test_mpb_requires_steric_parameters(gps, ctx):
+    p = synth.workload(4, n=32, count=2, margin=3.0, kind="nlpb")
+    el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+    with pytest.raises(gps.GpsError) as e:
+        ctx.pb_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), el, "mpb", T(np.zeros(p.grid.shape)))
+    assert e.value.status == gps.GPS_ERR_INVALID
+
+
+def test_full_surface_mpb(gps, ctx):
+    """Config-3 slab with the steric ionic charge (0.1 M, p = 0.74,
+    R = 3 angstrom), FP64 at full size: the oracle's fixed-point residual of
+    the full modified-PB equation at the GPU potential."""
+    p = synth.workload(3, kind="nlpb")
+    el_o = _steric(p.electrolyte)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.pb_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), _gps_el(gps, el_o, p.eps0), "mpb", phi,
+                       gps.default_opts(tol_outer=1e-10, max_iter=2000))
+    assert rep.status == 0 and rep.outer_iters > 1
+    ph = N(phi, p.grid.shape)
+    gam = oracle.pb.exclusion_from_eps(p.eps, p.eps0)
+    rions = oracle.pb.ionic_charge(ph, gam, el_o)
+    assert _fixed_point_residual(p, ph, rions=rions) < 1e-9
 
 
 # ---------------------------------------------------------------- edge cases
@@ -549,7 +647,8 @@ def test_df64_solves(gps, ctx, wl, kw, kind):
 
 
 def test_df64_nlpb(gps, ctx):
-    p = synth.workload(3, nxy=32, nz=64, count=8, kind="nlpb")
+    p = synth.workload(3, nxy=32, nz=96, count=8, kind="nlpb")
+    assert _has_solvent(p)
     el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
     phi = T(np.zeros(p.grid.shape))
     opts = gps.default_opts(tol_outer=1e-11, max_iter=3000, precision=gps.GPS_DF64)
