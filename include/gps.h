@@ -62,6 +62,29 @@ typedef enum { GPS_FP64 = 0, GPS_MIXED = 1, GPS_DF64 = 2, GPS_MIXED_DF64 = 3 } g
 typedef enum { GPS_GPE = 0, GPS_LPB = 1, GPS_NLPB = 2, GPS_MPB = 3 } gps_problem;
 typedef enum { GPS_OUTER_NEWTON = 0, GPS_OUTER_PRINTED = 1 } gps_outer_mode;
 
+/* Solver of the generalized Poisson equation (gps_opts.method; accepted by
+ * gps_gpe_solve and gps_gpe_solve_host only, with precision GPS_FP64 and
+ * warm_start 0; other methods than GPS_PCG return GPS_ERR_INVALID elsewhere).
+ *   GPS_PCG  Algorithm 2 with the preconditioner of Eq. (PCGdef) (default).
+ *   GPS_SC   Algorithm 1, the self-consistent iteration (Eqs. remap, rhoiter):
+ *            phi_k = S(rho/eps + rho_iter_k), rho~ = grad ln eps . grad phi_k / 4 pi,
+ *            rho_iter_(k+1) = eta rho~ + (1 - eta) rho_iter_k (opts.eta).
+ *   GPS_PSD  Algorithm 2 with beta = 0 and the preconditioner of Eq. (PrePSD),
+ *            eps lap v = r; step opts.alpha, or (alpha = 0) the steepest-
+ *            descent step (v, r) / (v, A v); with opts.diis = m >= 2, Pulay's
+ *            DIIS over the last m iterates before every step.
+ * Both comparison solvers take grad ln eps by the order-16 central first
+ * derivative (Sec. "Numerical results") and the Laplacian that the vacuum
+ * solve inverts: A phi = eps (lap_S phi + grad ln eps . grad phi), a
+ * discretization of Eq. (GPe) that differs from Algorithm 2's at the level of
+ * the discretization error.  They stop on ||r||_2 <= max(tol_abs, tol_rel
+ * ||r_0||_2) with r = -4 pi rho - A phi (SC: r_k = -4 pi eps (rho~ - rho_iter_k),
+ * the residual of phi_k), for periodic BC measured modulo its component along
+ * eps; rep->iters counts vacuum solves.  Periodic axes need at least 8
+ * points.  One vacuum solve and one order-16 stencil pass per iteration. */
+typedef enum { GPS_PCG = 0, GPS_SC = 1, GPS_PSD = 2 } gps_method;
+#define GPS_MAX_DIIS 8
+
 /* Uniform orthorhombic grid.  nx, ny, nz >= 4; each padded FFT length
  * (2n on free axes, n on periodic axes) must factor into 2, 3 and 5, be even
  * and be at most 4096.  Sec. "Numerical results" (orthorhombic grid of
@@ -106,7 +129,7 @@ typedef struct {
   int max_iter;          /* PCG iterations per solve (inner solves for NLPB) */
   int max_outer;         /* NLPB outer steps */
   double tol_outer;      /* NLPB outer tolerance on the ionic-charge residual */
-  double eta;            /* NLPB mixing parameter (printed Algorithm 4) */
+  double eta;            /* mixing: NLPB printed Algorithm 4; GPS_SC rho_iter (Algorithm 1) */
   int outer_mode;        /* gps_outer_mode */
   double forcing;        /* NLPB Newton: relative inner tolerance cap (e.g. 1e-2) */
   int precision;         /* gps_precision */
@@ -121,6 +144,9 @@ typedef struct {
                             (a warm start of Algorithm 2).  Every solve with warm_start set
                             keeps eps, phi and b - r on the device for the next one (three
                             more grid-sized arrays in the context).  Otherwise a cold start. */
+  int method;            /* gps_method (GPS_PCG) */
+  double alpha;          /* GPS_PSD: fixed step length; 0 = steepest-descent step */
+  int diis;              /* GPS_PSD: DIIS history length 0..GPS_MAX_DIIS (0 and 1: plain PSD) */
 } gps_opts;
 
 typedef struct {
@@ -144,7 +170,8 @@ typedef struct gps_ctx gps_ctx;
 
 /* Fill *opts with defaults: tol_abs 1e-10, tol_rel 0, max_iter 500,
  * max_outer 100, tol_outer 1e-10, eta 0.6, Newton outer mode, forcing 1e-2,
- * FP64, mixed_switch 1e-2, certify 0, warm_start 0. */
+ * FP64, mixed_switch 1e-2, certify 0, warm_start 0, method GPS_PCG (alpha 0,
+ * diis 0). */
 void gps_default_opts(gps_opts* opts);
 
 /* Human-readable name of a status code (static storage). */
@@ -295,14 +322,16 @@ int gps_vacuum_solve_noalloc(const gps_grid* grid, const double* sigma_dev, doub
 /* Instrumentation.  gps_set_profiling(ctx, mask): every kernel of a kind
  * whose bit is set in `mask` that the solve entry points launch is
  * bracketed by CUDA events on the call's stream, and the elapsed times are
- * collected when the call returns (mask 0 turns profiling off, 0xFF times
+ * collected when the call returns (mask 0 turns profiling off, 0x3FF times
  * every kind).  Kernel kinds: 0 x_fwd, 1 y_fwd, 2 z (forward, Green's
- * multiply, inverse), 3 y_inv, 4 x_inv, 5 update_p, 6 update_r, 7 setup.
+ * multiply, inverse), 3 y_inv, 4 x_inv, 5 update_p, 6 update_r, 7 setup,
+ * 8 stencil (the order-16 passes of GPS_SC / GPS_PSD), 9 sc_vector (their
+ * vector updates and DIIS).
  * Launches that return at once because the PCG had already converged are
  * not counted.  gps_get_profile writes per kind the launch count and the
  * total milliseconds accumulated since the last reset (arrays of
  * GPS_PROFILE_KINDS entries). */
-#define GPS_PROFILE_KINDS 8
+#define GPS_PROFILE_KINDS 10
 int gps_set_profiling(gps_ctx* ctx, int mask);
 int gps_get_profile(gps_ctx* ctx, long long* launches, double* total_ms, int reset);
 

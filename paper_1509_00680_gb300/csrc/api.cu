@@ -109,6 +109,22 @@ Fd16 fd16_coeffs() {
   return c;
 }
 
+// Order-16 central first-derivative coefficients (exact formula, long double):
+// f'(x) ~ (1/h) sum_j d_j (f(x + jh) - f(x - jh)),
+// d_j = (-1)^(j+1) (8!)^2 / (j (8-j)! (8+j)!).
+void fd16_first_coeffs(double* d) {
+  auto fact = [](int n) {
+    long double f = 1;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+  };
+  d[0] = 0.0;
+  for (int j = 1; j <= 8; ++j) {
+    long double v = fact(8) * fact(8) / ((long double)j * fact(8 - j) * fact(8 + j));
+    d[j] = (double)(j % 2 == 0 ? -v : v);
+  }
+}
+
 // Even (cosine) transform matrix C[k][j] = w_j cos(2 pi j k / M) * scale,
 // j = 0..M/2, k = 0..K-1, w_0 = w_(M/2) = 1, otherwise 2.
 std::vector<double> cosine_matrix(int M, int K, double scale) {
@@ -161,6 +177,19 @@ int validate_steric(const gps_electrolyte* el) {
   if (!el || !(el->packing > 0)) return GPS_ERR_INVALID;
   for (int s = 0; s < el->nspecies; ++s)
     if (!(el->radius_angstrom[s] > 0)) return GPS_ERR_INVALID;
+  return GPS_OK;
+}
+
+// gps_opts.method: the comparison solvers take GPe, FP64, cold starts, and
+// periodic axes of at least 8 points (the order-16 stencil wraps once).
+int validate_method(const gps_opts& o, int kind, const gps_grid* g) {
+  if (o.method == GPS_PCG) return GPS_OK;
+  if (o.method != GPS_SC && o.method != GPS_PSD) return GPS_ERR_INVALID;
+  if (kind != GPS_GPE || o.precision != GPS_FP64 || o.warm_start) return GPS_ERR_INVALID;
+  if (o.method == GPS_SC && !(o.eta > 0.0 && o.eta <= 1.0)) return GPS_ERR_INVALID;
+  if (o.method == GPS_PSD && (!(o.alpha >= 0.0) || o.diis < 0 || o.diis > GPS_MAX_DIIS)) return GPS_ERR_INVALID;
+  const bool pxy = g->bc != GPS_BC_FREE, pz = g->bc == GPS_BC_PERIODIC;
+  if ((pxy && (g->nx < 8 || g->ny < 8)) || (pz && g->nz < 8)) return GPS_ERR_INVALID;
   return GPS_OK;
 }
 
@@ -476,6 +505,18 @@ struct Request {
 
 namespace {
 
+// Work arrays of the comparison solvers (Algorithm 1, PSD, DIIS) on slot 0
+// of a direct pool, allocated on first use.
+struct ScWork {
+  double *gx = nullptr, *gy = nullptr, *gz = nullptr, *isc = nullptr, *tmp = nullptr;
+  double *a = nullptr, *b = nullptr, *c = nullptr, *d = nullptr;
+  double *hist = nullptr;   // DIIS ring: phi, r, v blocks of hist_m * n
+  int hist_m = 0;
+  double *part = nullptr, *dpart = nullptr, *small = nullptr;
+  unsigned int* cnt = nullptr;
+  int pstride = 0;
+};
+
 struct Pool {
   std::shared_ptr<Shape> shape;
   int cap = 1;
@@ -503,6 +544,7 @@ struct Pool {
   bool ws_valid = false;
   int ws_kind = -1;
   gps_electrolyte ws_el{};
+  ScWork sc;
   DevMem mem;
 
   ~Pool() {
@@ -1089,6 +1131,7 @@ struct Engine {
       if (v == GPS_OK && r->req.kind != GPS_GPE) v = validate_el(&r->req.el);
       if (v == GPS_OK && (r->req.kind < GPS_GPE || r->req.kind > GPS_MPB)) v = GPS_ERR_INVALID;
       if (v == GPS_OK && r->req.kind == GPS_MPB) v = validate_steric(&r->req.el);
+      if (v == GPS_OK && r->req.opts.method != GPS_PCG) v = GPS_ERR_INVALID;   // single solves only
       if (v == GPS_OK && (!r->req.rho_host || !r->req.eps_host || !r->req.phi_host)) v = GPS_ERR_INVALID;
       if (v != GPS_OK) {
         r->status = v;
@@ -1259,6 +1302,164 @@ int solve_direct(Pool& P, const double* rho, const double* eps, double* phi, int
   P.f.phi = P.own_phi;
   fill_report(rep, P.st_host[0], t0);
   return P.st_host[0].status;
+}
+
+// Comparison solvers of the GPe (gps_opts.method GPS_SC / GPS_PSD) on slot 0
+// of a direct pool: the FP64 spectrum pipeline is the vacuum solve of every
+// iteration, the kernels of sc.cu the rest.  Iterations are launched in
+// growing chunks; the slot's phase turns every later launch into a no-op
+// once the solve has converged.
+int solve_comparison(Pool& P, const double* rho, const double* eps, double* phi, const gps_opts& o,
+                     gps_report* rep, cudaStream_t st, double t0) {
+  const Shape& S = *P.shape;
+  const gps_grid& g = S.grid;
+  const size_t n = P.n;
+  ScWork& w = P.sc;
+  if (!w.gx) {
+    w.pstride = sc_blocks(n) + 32;
+    w.gx = P.mem.alloc<double>(n);
+    w.gy = P.mem.alloc<double>(n);
+    w.gz = P.mem.alloc<double>(n);
+    w.isc = P.mem.alloc<double>(n);
+    w.tmp = P.mem.alloc<double>(n);
+    w.a = P.mem.alloc<double>(n);
+    w.b = P.mem.alloc<double>(n);
+    w.c = P.mem.alloc<double>(n);
+    w.d = P.mem.alloc<double>(n);
+    w.part = P.mem.alloc<double>(4 * (size_t)w.pstride);
+    w.dpart = P.mem.alloc<double>((size_t)kMaxDiis * w.pstride);
+    w.small = P.mem.alloc<double>(128);
+    w.cnt = P.mem.alloc<unsigned int>(8);
+    ck(cudaMemsetAsync(w.cnt, 0, 8 * sizeof(unsigned int), st));
+  }
+  const bool psd = o.method == GPS_PSD;
+  const int m = psd && o.diis >= 2 ? o.diis : 0;
+  if (m > w.hist_m) {
+    w.hist = P.mem.alloc<double>(3 * (size_t)m * n);
+    w.hist_m = m;
+  }
+  ScArgs a{};
+  a.S = P.st;
+  a.part = w.part;
+  a.dpart = w.dpart;
+  a.pstride = w.pstride;
+  a.cnt = w.cnt;
+  a.eps = eps;
+  a.rho = rho;
+  a.phi = phi;
+  a.gx = w.gx;
+  a.gy = w.gy;
+  a.gz = w.gz;
+  a.isc = w.isc;
+  a.tmp = w.tmp;
+  a.rho_eps = w.a;
+  a.rho_iter = w.b;
+  a.src = w.c;
+  a.hist_m = m;
+  a.hist_phi = w.hist;
+  a.hist_r = m ? w.hist + (size_t)m * n : nullptr;
+  a.hist_v = m ? w.hist + 2 * (size_t)m * n : nullptr;
+  a.hist_mr = w.small;
+  a.diis_B = w.small + 16;
+  a.diis_c = w.small + 16 + kMaxDiis * kMaxDiis;
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.nz = g.nz;
+  a.perx = g.bc != GPS_BC_FREE;
+  a.pery = g.bc != GPS_BC_FREE;
+  a.perz = g.bc == GPS_BC_PERIODIC;
+  a.ihx = 1.0 / g.hx;
+  a.ihy = 1.0 / g.hy;
+  a.ihz = 1.0 / g.hz;
+  a.n = n;
+  a.periodic = g.bc == GPS_BC_PERIODIC;
+  a.inv_n = 1.0 / (double)n;
+  fd16_first_coeffs(a.d);
+  a.alpha = o.alpha;
+
+  SlotState s{};
+  s.kind = GPS_GPE;
+  s.phase = PH_ITER;
+  s.spec = s.spec_hi = SPEC_FP64;
+  s.max_iter = o.max_iter;
+  s.tol_abs = o.tol_abs;
+  s.tol_rel = o.tol_rel;
+  s.eta = o.eta;
+  s.cert = -1.0;
+  P.slot_req[0] = reinterpret_cast<Request*>(&P);   // marks slot 0 busy
+  put_state(P, 0, s, st);
+  put_active(P, st);
+
+  // PSD vectors: plain, phi (the output) and r, v, A v; DIIS, the ring plus
+  // the combination phi_w, r_w, v_w and its A v.
+  double *r = w.a, *v = w.b, *Av = w.c;
+  double *phi_w = w.a, *r_w = w.b, *v_w = w.c, *Av_w = w.d;
+  const Batch b = batch_of(P, PH_ITER, SPEC_FP64);
+  const Batch bt{};   // profiling records only
+  // runs launch(a') with a' = a plus the acted flag of the profiling record
+  auto prof = [&](int kind, auto&& launch) {
+    timed(kind, bt, st, [&](const Batch& bb) {
+      ScArgs aa = a;
+      aa.acted = bb.acted;
+      launch(aa);
+    });
+  };
+  prof(7, [&](const ScArgs& aa) {
+    if (!psd) launch_sc_prep(aa, 0, nullptr, nullptr, st);
+    else if (!m) launch_sc_prep(aa, 1, phi, r, st);
+    else launch_sc_prep(aa, 1, aa.hist_phi, aa.hist_r, st);
+  });
+  PipeArgs pa{};
+  pa.table = S.table;
+  pa.slot_k0 = 0;
+  auto iteration = [&](int k) {
+    if (!psd) {
+      pa.in = w.c;
+      pa.in_scale = nullptr;
+      pa.out = phi;
+      pipeline<double2>(P, b, pa, st);
+      prof(8, [&](const ScArgs& aa) { launch_sc_step(aa, st); });
+    } else if (!m) {
+      pa.in = r;
+      pa.in_scale = w.isc;
+      pa.out = v;
+      pipeline<double2>(P, b, pa, st);
+      prof(8, [&](const ScArgs& aa) { launch_psd_av(aa, v, r, Av, 0, st); });
+      prof(9, [&](const ScArgs& aa) { launch_psd_update(aa, phi, r, v, Av, phi, r, -1, st); });
+    } else {
+      const int j = k % m, cnt = std::min(k + 1, m), jn = (k + 1) % m;
+      pa.in = a.hist_r + (size_t)j * n;
+      pa.in_scale = w.isc;
+      pa.out = a.hist_v + (size_t)j * n;
+      pipeline<double2>(P, b, pa, st);
+      DiisSlots sl{};
+      sl.cnt = cnt;
+      for (int q = 0; q < cnt; ++q) sl.slot[q] = (k - cnt + 1 + q) % m;
+      prof(9, [&](const ScArgs& aa) { launch_diis(aa, sl, phi_w, r_w, v_w, st); });
+      prof(8, [&](const ScArgs& aa) { launch_psd_av(aa, v_w, r_w, Av_w, 1, st); });
+      prof(9, [&](const ScArgs& aa) {
+        launch_psd_update(aa, phi_w, r_w, v_w, Av_w, aa.hist_phi + (size_t)jn * n, aa.hist_r + (size_t)jn * n,
+                          jn, st);
+      });
+    }
+  };
+  int k = 0, chunk = 4;
+  for (;;) {
+    for (int c = 0; c < chunk && k < o.max_iter; ++c) iteration(k++);
+    get_states(P, st);
+    ck(cudaStreamSynchronize(st));
+    if (t_prof) t_prof->resolve();
+    if (P.st_host[0].phase != PH_ITER || k >= o.max_iter) break;
+    chunk = std::min(2 * chunk, 32);
+  }
+  const SlotState& f = P.st_host[0];
+  if (m) {
+    const int last = f.iter % m;
+    ck(cudaMemcpyAsync(phi, a.hist_phi + (size_t)last * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  fill_report(rep, f, t0);
+  P.slot_req[0] = nullptr;
+  return f.status;
 }
 
 Pool* direct_pool(gps_ctx* ctx, const gps_grid* gr, cudaStream_t st) {
@@ -1447,12 +1648,14 @@ int gps_pb_solve(gps_ctx* ctx, const gps_grid* grid, const double* rho, const do
   if (kind != GPS_GPE && (v = validate_el(el)) != GPS_OK) return v;
   gps_opts o;
   if (opts) o = *opts; else gps_default_opts(&o);
+  if ((v = validate_method(o, kind, grid)) != GPS_OK) return v;
   cudaStream_t st = (cudaStream_t)stream;
   GPS_GUARD_BEGIN
   cudaSetDevice(ctx->device);
   ProfScope prof_scope(ctx);
   Pool* P = direct_pool(ctx, grid, st);
-  int s = solve_direct(*P, rho, eps, phi, kind, el, o, rep, st, t0);
+  int s = o.method == GPS_PCG ? solve_direct(*P, rho, eps, phi, kind, el, o, rep, st, t0)
+                              : solve_comparison(*P, rho, eps, phi, o, rep, st, t0);
   s = finish(s, st);
   if (rep) rep->time_ms = now_ms() - t0;
   return s;
@@ -1477,6 +1680,7 @@ int gps_pb_solve_host(gps_ctx* ctx, const gps_grid* grid, const double* rho_h, c
   if (kind != GPS_GPE && (v = validate_el(el)) != GPS_OK) return v;
   gps_opts o;
   if (opts) o = *opts; else gps_default_opts(&o);
+  if ((v = validate_method(o, kind, grid)) != GPS_OK) return v;
   cudaStream_t st = (cudaStream_t)stream;
   GPS_GUARD_BEGIN
   cudaSetDevice(ctx->device);
@@ -1485,7 +1689,8 @@ int gps_pb_solve_host(gps_ctx* ctx, const gps_grid* grid, const double* rho_h, c
   const size_t b = P->n * sizeof(double);
   ck(cudaMemcpyAsync(P->own_rho, rho_h, b, cudaMemcpyHostToDevice, st));
   ck(cudaMemcpyAsync(P->own_eps, eps_h, b, cudaMemcpyHostToDevice, st));
-  int s = solve_direct(*P, P->own_rho, P->own_eps, P->own_phi, kind, el, o, rep, st, t0);
+  int s = o.method == GPS_PCG ? solve_direct(*P, P->own_rho, P->own_eps, P->own_phi, kind, el, o, rep, st, t0)
+                              : solve_comparison(*P, P->own_rho, P->own_eps, P->own_phi, o, rep, st, t0);
   ck(cudaMemcpyAsync(phi_h, P->own_phi, b, cudaMemcpyDeviceToHost, st));
   s = finish(s, st);
   if (rep) rep->time_ms = now_ms() - t0;

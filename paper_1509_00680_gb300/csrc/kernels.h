@@ -58,4 +58,59 @@ void launch_free_ghat(double* out, int mx, int my, int mz, double dkx, double dk
 void launch_axis_matrix(const double* in, double* out, const double* C, int A, int J, int B, int K,
                         cudaStream_t st);
 
+// ---- comparison solvers (sc.cu): Algorithm 1 (SC), PSD, PSD + DIIS ------
+
+constexpr int kMaxDiis = 8;   // GPS_MAX_DIIS
+
+// Ring slots of the DIIS history in use, oldest first (the newest last).
+struct DiisSlots {
+  int cnt;
+  int slot[kMaxDiis];
+};
+
+// Everything the comparison-solver kernels touch.  Periodic axes must have
+// at least 8 points (the order-16 stencil wraps once).
+struct ScArgs {
+  SlotState* S;                 // slot 0 of the pool: phase, scalars, convergence
+  double* part;                 // 4 x pstride reduction partials
+  double* dpart;                // kMaxDiis x pstride partials (DIIS dot products)
+  int pstride;
+  unsigned int* cnt;            // 5 reduction tickets (zero between launches)
+  const double *eps, *rho;
+  double* phi;                  // SC output (PSD: see the launchers)
+  double *gx, *gy, *gz;         // grad ln eps (order 16)
+  double* isc;                  // -1 / (4 pi eps)
+  double* tmp;                  // ln eps during setup
+  double *rho_eps, *rho_iter, *src;   // SC
+  double *hist_phi, *hist_r, *hist_v; // DIIS ring, hist_m slots of n each
+  double* hist_mr;              // <r/eps> of every ring slot; [kMaxDiis]: of the combination
+  double* diis_B;               // kMaxDiis x kMaxDiis Gram matrix (ring-slot indexed)
+  double* diis_c;               // coefficients of the current combination
+  int hist_m;
+  int nx, ny, nz, perx, pery, perz;
+  double ihx, ihy, ihz;         // 1 / h
+  size_t n;
+  int periodic;
+  double inv_n;
+  double d[9];                  // order-16 first-derivative coefficients d_1..d_8
+  double alpha;                 // PSD: fixed step, 0 = steepest descent
+  int* acted;                   // optional: set by a launch that did work (profiling)
+};
+
+int sc_blocks(size_t n);
+// Setup of SC (psd = 0) or PSD (psd = 1; phi0 = 0 and r0 = -4 pi rho are
+// written to the given arrays) and g = grad ln eps.
+void launch_sc_prep(const ScArgs& a, int psd, double* phi0, double* r0, cudaStream_t st);
+// SC step after the vacuum solve phi = S(src).
+void launch_sc_step(const ScArgs& a, cudaStream_t st);
+// PSD: A v and alpha (diis: the mean <r/eps> of the DIIS combination).
+void launch_psd_av(const ScArgs& a, const double* v, const double* r, double* Av, int diis, cudaStream_t st);
+// PSD: phi_out = phi + alpha v, r_out = r - alpha A v, convergence; hist_slot
+// >= 0 records <r_out/eps> for that DIIS ring slot.
+void launch_psd_update(const ScArgs& a, const double* phi, const double* r, const double* v, const double* Av,
+                       double* phi_out, double* r_out, int hist_slot, cudaStream_t st);
+// DIIS: Gram row of the newest v, coefficients, combination into phi_w, r_w, v_w.
+void launch_diis(const ScArgs& a, const DiisSlots& sl, double* phi_w, double* r_w, double* v_w,
+                 cudaStream_t st);
+
 }  // namespace gps

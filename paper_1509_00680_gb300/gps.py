@@ -19,6 +19,9 @@ GPS_BC_FREE, GPS_BC_PERIODIC, GPS_BC_SURFACE = 0, 1, 2
 GPS_FP64, GPS_MIXED, GPS_DF64, GPS_MIXED_DF64 = 0, 1, 2, 3
 GPS_GPE, GPS_LPB, GPS_NLPB, GPS_MPB = 0, 1, 2, 3
 GPS_OUTER_NEWTON, GPS_OUTER_PRINTED = 0, 1
+GPS_PCG, GPS_SC, GPS_PSD = 0, 1, 2
+GPS_MAX_DIIS = 8
+METHOD = {"pcg": GPS_PCG, "sc": GPS_SC, "psd": GPS_PSD}
 GPS_MAX_SPECIES = 8
 KIND = {"gpe": GPS_GPE, "lpb": GPS_LPB, "nlpb": GPS_NLPB, "mpb": GPS_MPB}
 
@@ -42,7 +45,8 @@ class gps_opts(ctypes.Structure):
                 ("tol_outer", ctypes.c_double), ("eta", ctypes.c_double),
                 ("outer_mode", ctypes.c_int), ("forcing", ctypes.c_double),
                 ("precision", ctypes.c_int), ("mixed_switch", ctypes.c_double),
-                ("certify", ctypes.c_int), ("warm_start", ctypes.c_int)]
+                ("certify", ctypes.c_int), ("warm_start", ctypes.c_int),
+                ("method", ctypes.c_int), ("alpha", ctypes.c_double), ("diis", ctypes.c_int)]
 
 
 class gps_report(ctypes.Structure):
@@ -98,8 +102,9 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "gps_kernel_launches": (ctypes.c_ulonglong, []),
 }
-GPS_PROFILE_KINDS = 8
-PROFILE_KINDS = ["x_fwd", "y_fwd", "z", "y_inv", "x_inv", "update_p", "update_r", "other"]
+GPS_PROFILE_KINDS = 10
+PROFILE_KINDS = ["x_fwd", "y_fwd", "z", "y_inv", "x_inv", "update_p", "update_r", "other", "stencil",
+                 "sc_vector"]
 
 _lib = None
 
