@@ -233,6 +233,7 @@ def run_ours(args, ws, rank, local):
                                                       total_ms / args.steps, precision=gps.GPS_MIXED_DF64)
     warm = None if args.no_mixed else run_warm(gps, local, p, g, rho, eps, flush)
     nonlinear = None if args.no_nonlinear else run_nonlinear(gps, local, flush)
+    comparison = None if args.no_comparison else run_comparison(gps, local, flush)
     serving = None if args.no_serving else run_serving(gps, local, args)
 
     # roofline of the dominant kernel (largest share of kernel time in warm-up)
@@ -258,6 +259,7 @@ def run_ours(args, ws, rank, local):
         "mixed_df64": mixed_df64,
         "warm_start": warm,
         "nonlinear": nonlinear,
+        "comparison": comparison,
         "serving": serving,
         "roofline": roof,
         "gpu_launches": int(launches),
@@ -372,6 +374,61 @@ def run_nonlinear(gps, device, flush):
         out[name] = {"ms": e0.elapsed_time(e1), "status": rep.status, "outer_iters": rep.outer_iters,
                      "pcg_iters": rep.iters, "fp64_iters": rep.fp64_iters,
                      "outer_res": rep.outer_res, "fixed_point_res": rep.fixed_point_res}
+    ctx.close()
+    return out
+
+
+# FP64 pipe operations per grid point of the stencil kernels (gps_opts.method
+# GPS_SC / GPS_PSD): 3 axes x 8 pairs x (subtract + FMA) = 48 for the
+# order-16 derivatives, 8 for grad ln eps . grad u, the rest for the
+# method's own update and the three residual sums (SC step: 66; PSD A v: 62).
+STENCIL_OPS = {"sc": 66, "psd": 62}
+FP64_PIPE_GOPS = 152 * 2 * 2.07   # 2 FP64 operations per clock per SM at 2.07 GHz
+
+
+def run_comparison(gps, device, flush):
+    """Algorithm 1 (SC, eta = 0.6), PSD + DIIS (m = 6) and Algorithm 2 on
+    the 128^3 periodic workload, each to ||r|| <= 1e-10 ||r_0|| in its own
+    discretization (FP64).  Per method: time per solve, iterations, time per
+    iteration, and the order-16 stencil kernel's time per launch against the
+    FP64-pipe peak (the kernel is FP64-pipe bound on GB300)."""
+    import torch
+    import synth
+    p = synth.workload(2)
+    g = gps.grid_from(p.grid)
+    rho = torch.from_numpy(p.rho.ravel()).to(device)
+    eps = torch.from_numpy(p.eps.ravel()).to(device)
+    ctx = gps.Context(device)
+    stream = torch.cuda.current_stream()
+    out = {"workload": p.name, "tol_rel": 1e-10}
+    methods = {"pcg": dict(method=gps.GPS_PCG), "sc": dict(method=gps.GPS_SC, eta=0.6),
+               "psd_diis6": dict(method=gps.GPS_PSD, diis=6)}
+    for name, kw in methods.items():
+        o = gps.default_opts(tol_abs=0.0, tol_rel=1e-10, max_iter=3000, **kw)
+        phi = torch.zeros_like(rho)
+        ctx.gpe_solve(g, rho, eps, phi, o)          # plans, tuning, work arrays
+        ctx.set_profiling(["stencil"] if name != "pcg" else None)
+        ctx.get_profile(reset=True)
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.profiler.start()           # ncu --profile-from-start off: the timed solves
+        e0.record(stream)
+        rep = ctx.gpe_solve(g, rho, eps, phi, o)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.profiler.stop()
+        ms = e0.elapsed_time(e1)
+        prof = ctx.get_profile(reset=True)
+        ctx.set_profiling(None)
+        row = {"ms": ms, "iters": rep.iters, "ms_per_iter": ms / max(rep.iters, 1), "status": rep.status,
+               "res_rel": rep.res / rep.res0 if rep.res0 else 0.0}
+        if name != "pcg":
+            n_l, t_l = prof["stencil"]
+            avg = t_l / max(n_l, 1)
+            ops = STENCIL_OPS["sc" if name == "sc" else "psd"] * p.grid.npts
+            row["stencil"] = {"launches": n_l, "avg_ms": avg, "fp64_gops": ops / (avg / 1e3) / 1e9,
+                              "frac_of_fp64_pipe": ops / (avg / 1e3) / 1e9 / FP64_PIPE_GOPS}
+        out[name] = row
     ctx.close()
     return out
 
@@ -649,6 +706,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-nonlinear", action="store_true")
+    ap.add_argument("--no-comparison", action="store_true")
     ap.add_argument("--clocks-log", default=None, help="keep the nvidia-smi samples of the timed region here")
     ap.add_argument("--serving-count", type=int, default=24)
     ap.add_argument("--passes", default=None, choices=sorted(PASS_CASES),

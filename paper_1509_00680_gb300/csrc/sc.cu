@@ -32,8 +32,6 @@
 
 namespace gps {
 
-namespace {
-
 constexpr int kT = 256;
 
 #define SC_STRIDE(i, n) \
@@ -49,8 +47,13 @@ __device__ __forceinline__ double proj_norm2(double A, double B, double C, doubl
 }
 
 // g . grad u at point idx = (i, j, k), order-16 central differences.
+// grad ln eps is exactly zero wherever eps is flat over the stencil (inside
+// the cavities, in the bulk solvent): the product is then zero without the
+// differences, which are the kernel's FP64 work and its neighbour loads.
 __device__ __forceinline__ double g_dot_grad(const double* __restrict__ u, size_t idx, int i, int j, int k,
                                              const ScArgs& a) {
+  const double gx = a.gx[idx], gy = a.gy[idx], gz = a.gz[idx];
+  if (gx == 0.0 && gy == 0.0 && gz == 0.0) return 0.0;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const double* row = u + (idx - i);
   const size_t sy = nx, sz = (size_t)nx * ny;
@@ -72,7 +75,7 @@ __device__ __forceinline__ double g_dot_grad(const double* __restrict__ u, size_
     dy = fma(d, u[bxz + (size_t)jp * sy] - u[bxz + (size_t)jm * sy], dy);
     dz = fma(d, u[bxy + (size_t)kp * sz] - u[bxy + (size_t)km * sz], dz);
   }
-  return a.gx[idx] * dx * a.ihx + a.gy[idx] * dy * a.ihy + a.gz[idx] * dz * a.ihz;
+  return gx * dx * a.ihx + gy * dy * a.ihy + gz * dz * a.ihz;
 }
 
 __device__ __forceinline__ void point_of(size_t idx, const ScArgs& a, int* i, int* j, int* k) {
@@ -274,7 +277,7 @@ __global__ void k_psd_update(ScArgs a, const double* __restrict__ phi, const dou
 
 // Pulay coefficients of the bordered system [[B, 1], [1^T, 0]] [c, mu] =
 // [0, 1] by Gaussian elimination with partial pivoting (thread 0).
-__device__ void diis_solve(const double* B, int cnt, const int* slots, double* c) {
+static __device__ void diis_solve(const double* B, int cnt, const int* slots, double* c) {
   double M[kMaxDiis + 1][kMaxDiis + 2];
   const int n = cnt + 1;
   for (int i = 0; i < cnt; ++i) {
@@ -400,8 +403,6 @@ __global__ void k_diis_combine(ScArgs a, DiisSlots sl, double* __restrict__ phi_
     v_w[i] = v;
   }
 }
-
-}  // namespace
 
 int sc_blocks(size_t n) {
   size_t b = (n + kT - 1) / kT;
