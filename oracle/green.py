@@ -29,13 +29,28 @@ surface   Periodic in x and y, free in z.  For each in-plane wavevector the
           (kz_j = 2 pi j / (2 n_z h_z)):
               S^ = 4 pi (1 - (-1)^j exp(-k L_z)) / (k^2 + kz_j^2),
           and S^ = 2 pi L_z^2 at k = kz = 0.
+
+wire      Periodic in z, free in x and y.  For each z wavevector kz the 2D
+          Green's function of the transverse problem, truncated at
+          rho = |(x, y)| <= R = sqrt((n_x h_x)^2 + (n_y h_y)^2), has the closed-form
+          transform (cylindrical truncation of Rozzi et al., Phys. Rev. B 73,
+          205119 (2006)):
+              kz != 0: g = 2 K0(|kz| rho),
+                  S^ = 4 pi / (k^2 + kz^2) [1 + k R J1(k R) K0(|kz| R) - |kz| R J0(k R) K1(|kz| R)]
+              kz = 0:  g = 2 ln(R / rho) (gauge: zero at rho = R),
+                  S^ = 4 pi (1 - J0(k R)) / k^2,  pi R^2 at k = 0,
+          with k = |(kx, ky)|.  As for the free kernel, S^ is sampled on a
+          grid 4x oversampled in x and y, taken to real space by a DCT-I per
+          axis (h_x h_y g_m, |m_d| <= n_d), and the aperiodic transverse
+          convolution is done cyclically on the 2n-padded x, y grid; along z
+          the source is used at its DFT wavevectors (no padding).
 """
 import math
 
 import numpy as np
 import scipy.fft as sfft
 
-BC_FREE, BC_PERIODIC, BC_SURFACE = 0, 1, 2
+BC_FREE, BC_PERIODIC, BC_SURFACE, BC_WIRE = 0, 1, 2, 3
 
 _WORKERS = -1   # scipy.fft: use every host core
 
@@ -85,6 +100,50 @@ def free_kernel_table(grid):
     return _rfftn(gfull).real
 
 
+def wire_transverse_hat(kperp, kz, R):
+    """Transform of the truncated transverse Green's function at |kz| (see the
+    module docstring); kperp an array."""
+    from scipy import special
+    kperp = np.asarray(kperp, dtype=float)
+    if kz == 0.0:
+        with np.errstate(divide="ignore", invalid="ignore"):
+            out = 4.0 * np.pi * (1.0 - special.j0(kperp * R)) / (kperp * kperp)
+        return np.where(kperp == 0.0, np.pi * R * R, out)
+    a = abs(kz) * R
+    x = kperp * R
+    return 4.0 * np.pi / (kperp * kperp + kz * kz) * (
+        1.0 + x * special.j1(x) * special.k0(a) - a * special.j0(x) * special.k1(a))
+
+
+def wire_kernel_table(grid, oversample=4):
+    """Wire kernel on the rfftn layout (nz, 2ny, nx+1) of the grid padded to
+    (nz, 2ny, 2nx)."""
+    nx, ny, nz = grid.nx, grid.ny, grid.nz
+    hx, hy, hz = grid.hx, grid.hy, grid.hz
+    R = math.sqrt((nx * hx) ** 2 + (ny * hy) ** 2)
+    Mx, My = oversample * nx, oversample * ny
+    for n, h, M in ((nx, hx, Mx), (ny, hy, My)):
+        if M * h < n * h + R:
+            raise ValueError("box aspect ratio too large for %dx oversampling" % oversample)
+    kx = 2.0 * np.pi * np.arange(Mx // 2 + 1) / (Mx * hx)
+    ky = 2.0 * np.pi * np.arange(My // 2 + 1) / (My * hy)
+    kperp = np.sqrt(ky[:, None] ** 2 + kx[None, :] ** 2)
+    kz = 2.0 * np.pi * np.fft.fftfreq(nz, d=hz)
+    idx = [np.minimum(np.arange(2 * n), 2 * n - np.arange(2 * n)) for n in (ny, nx)]
+    T = np.empty((nz, 2 * ny, nx + 1))
+    cache = {}
+    for j in range(nz):
+        key = abs(int(round(np.fft.fftfreq(nz)[j] * nz)))
+        if key not in cache:
+            Ghat = wire_transverse_hat(kperp, abs(kz[j]), R)
+            y = sfft.dct(Ghat, type=1, axis=0, workers=_WORKERS)
+            y = sfft.dct(y, type=1, axis=1, workers=_WORKERS)
+            g = y[:ny + 1, :nx + 1] / float(Mx * My)          # h_x h_y g_m
+            cache[key] = sfft.rfft2(g[np.ix_(idx[0], idx[1])], workers=_WORKERS).real
+        T[j] = cache[key]
+    return T
+
+
 def periodic_kernel_table(grid):
     """4 pi / |k|^2 (0 at k = 0) on the rfftn layout (nz, ny, nx//2+1)."""
     kx = 2.0 * np.pi * np.fft.rfftfreq(grid.nx, d=grid.hx)
@@ -129,6 +188,9 @@ class VacuumSolver:
         elif self.bc == BC_SURFACE:
             self.table = surface_kernel_table(grid)
             self.pshape = (2 * n[0], n[1], n[2])
+        elif self.bc == BC_WIRE:
+            self.table = wire_kernel_table(grid)
+            self.pshape = (n[0], 2 * n[1], 2 * n[2])
         else:
             raise ValueError("unknown boundary condition %r" % self.bc)
 

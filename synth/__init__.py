@@ -24,8 +24,8 @@ from dataclasses import dataclass, field
 import numpy as np
 from scipy.special import erf
 
-BC_FREE, BC_PERIODIC, BC_SURFACE = 0, 1, 2
-BC_NAMES = {BC_FREE: "free", BC_PERIODIC: "periodic", BC_SURFACE: "surface"}
+BC_FREE, BC_PERIODIC, BC_SURFACE, BC_WIRE = 0, 1, 2, 3
+BC_NAMES = {BC_FREE: "free", BC_PERIODIC: "periodic", BC_SURFACE: "surface", BC_WIRE: "wire"}
 EPS_WATER = 78.36
 
 
@@ -54,6 +54,8 @@ class Grid:
             return (True, True, True)
         if self.bc == BC_SURFACE:
             return (True, True, False)
+        if self.bc == BC_WIRE:
+            return (False, False, True)
         return (False, False, False)
 
     def lengths(self):

@@ -169,7 +169,7 @@ def test_surface_kernel_matches_quadrature_of_truncated_green():
         assert abs(T[jz, jy, jx] - 2 * val) < 1e-10 * max(1.0, abs(2 * val))
 
 
-@pytest.mark.parametrize("bc", [synth.BC_FREE, synth.BC_PERIODIC, synth.BC_SURFACE])
+@pytest.mark.parametrize("bc", [synth.BC_FREE, synth.BC_PERIODIC, synth.BC_SURFACE, synth.BC_WIRE])
 def test_preconditioner_symmetric_positive(bc):
     n = 12
     g = synth.Grid(n, n + 2, n - 2, 0.5, 0.45, 0.55, bc)
@@ -196,7 +196,7 @@ def _mild_problem(bc, n=10, lam=0.0, seed=5):
     return g, rho, eps, lam
 
 
-@pytest.mark.parametrize("bc", [synth.BC_FREE, synth.BC_PERIODIC, synth.BC_SURFACE])
+@pytest.mark.parametrize("bc", [synth.BC_FREE, synth.BC_PERIODIC, synth.BC_SURFACE, synth.BC_WIRE])
 @pytest.mark.parametrize("lam", [0.0, 0.7])
 def test_pcg_matches_dense_direct_solve(bc, lam):
     g, rho, eps, lam = _mild_problem(bc, lam=lam)
