@@ -234,6 +234,7 @@ def run_ours(args, ws, rank, local):
     warm = None if args.no_mixed else run_warm(gps, local, p, g, rho, eps, flush)
     nonlinear = None if args.no_nonlinear else run_nonlinear(gps, local, flush)
     comparison = None if args.no_comparison else run_comparison(gps, local, flush)
+    wire = None if args.no_wire else run_wire(gps, local, flush)
     serving = None if args.no_serving else run_serving(gps, local, args)
 
     # roofline of the dominant kernel (largest share of kernel time in warm-up)
@@ -260,6 +261,7 @@ def run_ours(args, ws, rank, local):
         "warm_start": warm,
         "nonlinear": nonlinear,
         "comparison": comparison,
+        "wire": wire,
         "serving": serving,
         "roofline": roof,
         "gpu_launches": int(launches),
@@ -429,6 +431,37 @@ def run_comparison(gps, device, flush):
             row["stencil"] = {"launches": n_l, "avg_ms": avg, "fp64_gops": ops / (avg / 1e3) / 1e9,
                               "frac_of_fp64_pipe": ops / (avg / 1e3) / 1e9 / FP64_PIPE_GOPS}
         out[name] = row
+    ctx.close()
+    return out
+
+
+def run_wire(gps, device, flush):
+    """Wire BC (periodic z, free x and y): GPe on a 128 x 128 x 256 chain of 8
+    cavities (radius 2.4 bohr, a pair of Gaussians in each), ||r|| <= 1e-10,
+    FP64 and mixed df64 spectra; one untimed solve first (table, tuning)."""
+    import torch
+    import synth
+    p = synth.wire_chain(n=128, nz=256, count=8, kind="gpe")
+    g = gps.grid_from(p.grid)
+    rho = torch.from_numpy(p.rho.ravel()).to(device)
+    eps = torch.from_numpy(p.eps.ravel()).to(device)
+    ctx = gps.Context(device)
+    stream = torch.cuda.current_stream()
+    out = {"workload": p.name, "grid": list(p.grid.shape), "padded": [2 * p.grid.nx, 2 * p.grid.ny, p.grid.nz]}
+    for name, prec in (("fp64", gps.GPS_FP64), ("mixed_df64", gps.GPS_MIXED_DF64)):
+        o = gps.default_opts(tol_abs=1e-10, max_iter=2000, precision=prec)
+        phi = torch.zeros_like(rho)
+        ctx.gpe_solve(g, rho, eps, phi, o)
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = ctx.gpe_solve(g, rho, eps, phi, o)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"ms": ms, "iters": rep.iters, "status": rep.status,
+                     "grid_pt_iter_per_s": p.grid.npts * rep.iters / (ms / 1e3),
+                     "certificate": rep.fixed_point_res}
     ctx.close()
     return out
 
@@ -707,6 +740,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-nonlinear", action="store_true")
     ap.add_argument("--no-comparison", action="store_true")
+    ap.add_argument("--no-wire", action="store_true")
     ap.add_argument("--clocks-log", default=None, help="keep the nvidia-smi samples of the timed region here")
     ap.add_argument("--serving-count", type=int, default=24)
     ap.add_argument("--passes", default=None, choices=sorted(PASS_CASES),

@@ -46,7 +46,9 @@ typedef enum {
 typedef enum {
   GPS_BC_FREE = 0,       /* isolated system: truncated-Coulomb vacuum kernel on a 2x padded grid */
   GPS_BC_PERIODIC = 1,   /* periodic cell: spectral 4 pi / k^2 kernel */
-  GPS_BC_SURFACE = 2     /* periodic in x and y, free in z (2x padded in z) */
+  GPS_BC_SURFACE = 2,    /* periodic in x and y, free in z (2x padded in z) */
+  GPS_BC_WIRE = 3        /* periodic in z, free in x and y (2x padded in x and y): the Coulomb
+                            kernel truncated at transverse radius sqrt((nx hx)^2 + (ny hy)^2) */
 } gps_bc;
 
 /* Arithmetic of the spectrum passes (the vacuum solve inside the
@@ -87,8 +89,10 @@ typedef enum { GPS_PCG = 0, GPS_SC = 1, GPS_PSD = 2 } gps_method;
 
 /* Uniform orthorhombic grid.  nx, ny, nz >= 4; each padded FFT length
  * (2n on free axes, n on periodic axes) must factor into 2, 3 and 5, be even
- * and be at most 4096.  Sec. "Numerical results" (orthorhombic grid of
- * uniform spacing). */
+ * and be at most 4096.  Free and wire BC also need 4 n_d h_d >= n_d h_d + R on
+ * every free axis d, R the truncation radius (the box diagonal; for wire the
+ * diagonal of the x-y cross-section), for the 4x oversampled kernel.
+ * Sec. "Numerical results" (orthorhombic grid of uniform spacing). */
 typedef struct {
   int nx, ny, nz;
   double hx, hy, hz;

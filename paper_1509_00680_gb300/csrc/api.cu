@@ -188,7 +188,8 @@ int validate_method(const gps_opts& o, int kind, const gps_grid* g) {
   if (kind != GPS_GPE || o.precision != GPS_FP64 || o.warm_start) return GPS_ERR_INVALID;
   if (o.method == GPS_SC && !(o.eta > 0.0 && o.eta <= 1.0)) return GPS_ERR_INVALID;
   if (o.method == GPS_PSD && (!(o.alpha >= 0.0) || o.diis < 0 || o.diis > GPS_MAX_DIIS)) return GPS_ERR_INVALID;
-  const bool pxy = g->bc != GPS_BC_FREE, pz = g->bc == GPS_BC_PERIODIC;
+  const bool pxy = g->bc == GPS_BC_PERIODIC || g->bc == GPS_BC_SURFACE;
+  const bool pz = g->bc == GPS_BC_PERIODIC || g->bc == GPS_BC_WIRE;
   if ((pxy && (g->nx < 8 || g->ny < 8)) || (pz && g->nz < 8)) return GPS_ERR_INVALID;
   return GPS_OK;
 }
@@ -197,8 +198,9 @@ int validate_grid(const gps_grid* g) {
   if (!g) return GPS_ERR_INVALID;
   if (g->nx < 4 || g->ny < 4 || g->nz < 4) return GPS_ERR_INVALID;
   if (!(g->hx > 0) || !(g->hy > 0) || !(g->hz > 0)) return GPS_ERR_INVALID;
-  if (g->bc < GPS_BC_FREE || g->bc > GPS_BC_SURFACE) return GPS_ERR_INVALID;
-  const bool fx = g->bc == GPS_BC_FREE, fz = g->bc != GPS_BC_PERIODIC;
+  if (g->bc < GPS_BC_FREE || g->bc > GPS_BC_WIRE) return GPS_ERR_INVALID;
+  const bool fx = g->bc == GPS_BC_FREE || g->bc == GPS_BC_WIRE;
+  const bool fz = g->bc == GPS_BC_FREE || g->bc == GPS_BC_SURFACE;
   const int Px = fx ? 2 * g->nx : g->nx, Py = fx ? 2 * g->ny : g->ny, Pz = fz ? 2 * g->nz : g->nz;
   for (int P : {Px, Py, Pz})
     if (P % 2 || P > kMaxLen || !factorable(P)) return GPS_ERR_INVALID;
@@ -208,6 +210,11 @@ int validate_grid(const gps_grid* g) {
     if (4 * g->nx * g->hx < g->nx * g->hx + R || 4 * g->ny * g->hy < g->ny * g->hy + R ||
         4 * g->nz * g->hz < g->nz * g->hz + R)
       return GPS_ERR_INVALID;   // aspect ratio too large for the 4x oversampled kernel
+  }
+  if (g->bc == GPS_BC_WIRE) {
+    const double R = std::sqrt(std::pow(g->nx * g->hx, 2) + std::pow(g->ny * g->hy, 2));
+    if (4 * g->nx * g->hx < g->nx * g->hx + R || 4 * g->ny * g->hy < g->ny * g->hy + R)
+      return GPS_ERR_INVALID;   // transverse aspect ratio too large for the oversampled kernel
   }
   return GPS_OK;
 }
@@ -440,10 +447,59 @@ void build_free_table(Shape* S, cudaStream_t st) {
   ck(cudaGetLastError());
 }
 
+// Wire-BC table: per |kz| index, h_x h_y g on the (x, y) quadrant from the
+// 4x oversampled transform of the transversely truncated Green's function
+// (two even transforms), then the transform of its 2n-periodic extension
+// (two more); z needs none (periodic, DFT wavevectors).  Normalized by
+// 1/(Px Py Pz).  K0, K1 at kz R are evaluated here on the host (one pair per
+// kz); J0, J1 on the device.
+void build_wire_table(Shape* S, cudaStream_t st) {
+  const int nx = S->grid.nx, ny = S->grid.ny, nz = S->grid.nz;
+  const double hx = S->grid.hx, hy = S->grid.hy, hz = S->grid.hz;
+  const int Mx = 4 * nx, My = 4 * ny;
+  const int mx = Mx / 2 + 1, my = My / 2 + 1, mz = nz / 2 + 1;
+  const double R = std::sqrt(std::pow(nx * hx, 2) + std::pow(ny * hy, 2));
+  const double dkz = 2 * kPi / (nz * hz);
+  const int hxo = nx + 1, hyo = ny + 1;
+  std::vector<double> k0(mz, 0.0), k1(mz, 0.0);
+  for (int k = 1; k < mz; ++k) {
+    const double a = k * dkz * R;
+    // K0, K1 below the smallest double for a > ~700; their terms vanish there
+    if (a < 700.0) {
+      k0[k] = std::cyl_bessel_k(0.0, a);
+      k1[k] = std::cyl_bessel_k(1.0, a);
+    }
+  }
+  DevMem tmp;
+  auto up = [&](const std::vector<double>& h) {
+    double* d = tmp.alloc<double>(h.size());
+    ck(cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return d;
+  };
+  double* k0d = up(k0);
+  double* k1d = up(k1);
+  double* ghat = tmp.alloc<double>((size_t)mx * my * mz);
+  launch_wire_ghat(ghat, mx, my, mz, 2 * kPi / (Mx * hx), 2 * kPi / (My * hy), dkz, R, k0d, k1d, st);
+  double* cx = up(cosine_matrix(Mx, hxo, 1.0 / Mx));
+  double* cy = up(cosine_matrix(My, hyo, 1.0 / My));
+  double* t1 = tmp.alloc<double>((size_t)mz * my * hxo);
+  launch_axis_matrix(ghat, t1, cx, mz * my, mx, 1, hxo, st);
+  double* g = tmp.alloc<double>((size_t)mz * hyo * hxo);
+  launch_axis_matrix(t1, g, cy, mz, my, hxo, hyo, st);
+  double* dx = up(cosine_matrix(2 * nx, hxo, 1.0 / (2 * nx)));
+  double* dy = up(cosine_matrix(2 * ny, hyo, 1.0 / (2.0 * ny * nz)));
+  double* u1 = tmp.alloc<double>((size_t)mz * hyo * hxo);
+  launch_axis_matrix(g, u1, dx, mz * hyo, hxo, 1, hxo, st);
+  launch_axis_matrix(u1, S->table, dy, mz, hyo, hxo, hyo, st);
+  ck(cudaStreamSynchronize(st));
+  ck(cudaGetLastError());
+}
+
 std::shared_ptr<Shape> build_shape(const gps_grid* gr, cudaStream_t st) {
   auto S = std::make_shared<Shape>();
   S->grid = *gr;
-  const bool fx = gr->bc == GPS_BC_FREE, fz = gr->bc != GPS_BC_PERIODIC;
+  const bool fx = gr->bc == GPS_BC_FREE || gr->bc == GPS_BC_WIRE;
+  const bool fz = gr->bc == GPS_BC_FREE || gr->bc == GPS_BC_SURFACE;
   S->Px = fx ? 2 * gr->nx : gr->nx;
   S->Py = fx ? 2 * gr->ny : gr->ny;
   S->Pz = fz ? 2 * gr->nz : gr->nz;
@@ -479,6 +535,8 @@ std::shared_ptr<Shape> build_shape(const gps_grid* gr, cudaStream_t st) {
     launch_table_periodic(S->table, S->lap, S->Hx, hy, hz, dkx, dky, dkz, S->inv_p, st);
   } else if (gr->bc == GPS_BC_SURFACE) {
     launch_table_surface(S->table, S->Hx, hy, hz, dkx, dky, dkz, gr->nz * gr->hz, S->inv_p, st);
+  } else if (gr->bc == GPS_BC_WIRE) {
+    build_wire_table(S.get(), st);
   } else {
     build_free_table(S.get(), st);
   }
@@ -850,8 +908,9 @@ void launch_setup_group(Pool& P, cudaStream_t st) {
     pipeline<double2>(P, b, a, st);
   } else {
     const int per_xy = S.grid.bc == GPS_BC_SURFACE ? 1 : 0;   // surface: x, y wrap; z free
+    const int per_z = S.grid.bc == GPS_BC_WIRE ? 1 : 0;       // wire: z wraps; x, y free
     launch_fd16_q(b, P.f, S.grid.nx, S.grid.ny, S.grid.nz, S.grid.hx, S.grid.hy, S.grid.hz, per_xy,
-                  per_xy, 0, fd16_coeffs(), P.cap, st);
+                  per_xy, per_z, fd16_coeffs(), P.cap, st);
   }
 }
 
@@ -1365,9 +1424,9 @@ int solve_comparison(Pool& P, const double* rho, const double* eps, double* phi,
   a.nx = g.nx;
   a.ny = g.ny;
   a.nz = g.nz;
-  a.perx = g.bc != GPS_BC_FREE;
-  a.pery = g.bc != GPS_BC_FREE;
-  a.perz = g.bc == GPS_BC_PERIODIC;
+  a.perx = g.bc == GPS_BC_PERIODIC || g.bc == GPS_BC_SURFACE;
+  a.pery = a.perx;
+  a.perz = g.bc == GPS_BC_PERIODIC || g.bc == GPS_BC_WIRE;
   a.ihx = 1.0 / g.hx;
   a.ihy = 1.0 / g.hy;
   a.ihz = 1.0 / g.hz;

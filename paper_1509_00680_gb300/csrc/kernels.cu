@@ -635,6 +635,32 @@ __global__ void k_free_ghat(double* __restrict__ out, int mx, int my, int mz, do
   }
 }
 
+// Wire-BC transform of the transversely truncated Green's function on the
+// oversampled (kx, ky) quadrant for every |kz| index jz (cylindrical
+// truncation at R): kz != 0, 4 pi / (k^2 + kz^2) [1 + kR J1(kR) K0(kz R) -
+// kz R J0(kR) K1(kz R)] with K0(kz R), K1(kz R) given per jz; kz = 0 (gauge
+// 2 ln(R / rho)), 4 pi (1 - J0(kR)) / k^2, pi R^2 at k = 0.
+__global__ void k_wire_ghat(double* __restrict__ out, int mx, int my, int mz, double dkx, double dky,
+                            double dkz, double R, const double* __restrict__ k0R,
+                            const double* __restrict__ k1R) {
+  const size_t n = (size_t)mx * my * mz;
+  GRID_STRIDE(idx, n) {
+    const int i = (int)(idx % mx);
+    const int j = (int)((idx / mx) % my);
+    const int k = (int)(idx / ((size_t)mx * my));
+    const double kx = i * dkx, ky = j * dky, kz = k * dkz;
+    const double kp2 = kx * kx + ky * ky, x = sqrt(kp2) * R;
+    double v;
+    if (k == 0) {
+      v = (i == 0 && j == 0) ? kPi * R * R : 4.0 * kPi * (1.0 - j0(x)) / kp2;
+    } else {
+      const double a = kz * R;
+      v = 4.0 * kPi / (kp2 + kz * kz) * (1.0 + x * j1(x) * k0R[k] - a * j0(x) * k1R[k]);
+    }
+    out[idx] = v;
+  }
+}
+
 // Dense transform along the middle index of in[A][J][B] -> out[A][K][B]:
 // out[a][k][b] = sum_j C[k][j] in[a][j][b].  Used for the even (cosine)
 // transforms of the free-BC table.
@@ -791,6 +817,13 @@ void launch_free_ghat(double* out, int mx, int my, int mz, double dkx, double dk
   const size_t n = (size_t)mx * my * mz;
   count_launch();
   k_free_ghat<<<grid_blocks(n, kT), kT, 0, st>>>(out, mx, my, mz, dkx, dky, dkz, R);
+}
+
+void launch_wire_ghat(double* out, int mx, int my, int mz, double dkx, double dky, double dkz, double R,
+                      const double* k0R, const double* k1R, cudaStream_t st) {
+  const size_t n = (size_t)mx * my * mz;
+  count_launch();
+  k_wire_ghat<<<grid_blocks(n, kT), kT, 0, st>>>(out, mx, my, mz, dkx, dky, dkz, R, k0R, k1R);
 }
 
 void launch_axis_matrix(const double* in, double* out, const double* C, int A, int J, int B, int K,

@@ -55,6 +55,8 @@ void launch_table_surface(double* kern, int Hx, int hy, int hz, double dkx, doub
                           double Lz, double inv_n, cudaStream_t st);
 void launch_free_ghat(double* out, int mx, int my, int mz, double dkx, double dky, double dkz,
                       double R, cudaStream_t st);
+void launch_wire_ghat(double* out, int mx, int my, int mz, double dkx, double dky, double dkz, double R,
+                      const double* k0R, const double* k1R, cudaStream_t st);
 void launch_axis_matrix(const double* in, double* out, const double* C, int A, int J, int B, int K,
                         cudaStream_t st);
 

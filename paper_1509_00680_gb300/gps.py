@@ -15,7 +15,7 @@ from .build import LIB
 
 GPS_OK, GPS_ERR_INVALID, GPS_ERR_NOMEM, GPS_ERR_NOT_CONVERGED = 0, 1, 2, 3
 GPS_ERR_BREAKDOWN, GPS_ERR_TIMEOUT, GPS_ERR_CUDA, GPS_PENDING = 4, 5, 6, 7
-GPS_BC_FREE, GPS_BC_PERIODIC, GPS_BC_SURFACE = 0, 1, 2
+GPS_BC_FREE, GPS_BC_PERIODIC, GPS_BC_SURFACE, GPS_BC_WIRE = 0, 1, 2, 3
 GPS_FP64, GPS_MIXED, GPS_DF64, GPS_MIXED_DF64 = 0, 1, 2, 3
 GPS_GPE, GPS_LPB, GPS_NLPB, GPS_MPB = 0, 1, 2, 3
 GPS_OUTER_NEWTON, GPS_OUTER_PRINTED = 0, 1

@@ -295,6 +295,26 @@ def free_union(n=256, h=0.3, count=200, margin=10.0, kind="nlpb", conc=0.5, seed
                    charges=charges, spheres=spheres, tol_abs=1e-10)
 
 
+def wire_chain(n=32, nz=48, h=0.35, count=3, radius=2.4, conc=0.3, kind="lpb"):
+    """Wire BC (periodic z, free x and y): `count` cavities of radius `radius`
+    (Delta = 0.5) evenly spaced along z on the box axis, each holding a pair
+    of Gaussians, q = +-1 (sigma 0.9) and -q/2 (sigma 0.8), offset from the
+    centre; the cavities end well inside the free faces.  1:1 electrolyte at
+    `conc` mol/L and 300 K."""
+    g = Grid(n, n, nz, h, h, h, BC_WIRE)
+    c = n // 2 * h
+    L = nz * h
+    zs = [(2 * i + 1) * L / (2 * count) for i in range(count)]
+    eps = rigid_cavity(g, [(radius, (c, c, z)) for z in zs], 0.5)
+    charges = []
+    for i, z in enumerate(zs):
+        q = 1.0 if i % 2 == 0 else -1.0
+        charges += [(q, 0.9, (c - 0.6, c, z)), (-0.5 * q, 0.8, (c + 0.7, c + 0.3, z + 0.4))]
+    return Problem("wire_%s_%dx%dx%d" % (kind, n, n, nz), g, gaussian_charges(g, charges), eps, kind=kind,
+                   electrolyte=Electrolyte((1, -1), (conc, conc), 300.0), charges=charges,
+                   spheres=[(radius, (c, c, z)) for z in zs], tol_abs=1e-10)
+
+
 def serving_request(rng, edge, bc, kind, h=0.3):
     """One serving request: cubic grid of `edge` points, 2-80 charges placed
     by the periodic-cluster rules, 1:1 electrolyte with c ~ log-U[0.01, 1]

@@ -61,6 +61,8 @@ SMALL = [
     (synth.BC_PERIODIC, (30, 24, 20), (0.4, 0.45, 0.5)),
     (synth.BC_SURFACE, (16, 12, 10), (0.5, 0.5, 0.5)),
     (synth.BC_SURFACE, (20, 18, 24), (0.4, 0.4, 0.35)),
+    (synth.BC_WIRE, (12, 10, 16), (0.5, 0.45, 0.4)),
+    (synth.BC_WIRE, (20, 18, 24), (0.4, 0.4, 0.35)),
 ]
 
 
@@ -125,6 +127,7 @@ COLUMN = [
     (synth.BC_FREE, (16, 128, 20), (0.8, 0.1, 0.64)),       # y 256
     (synth.BC_PERIODIC, (12, 256, 512), (0.5, 0.3, 0.2)),   # y 256, z 512
     (synth.BC_SURFACE, (8, 6, 512), (0.5, 0.5, 0.1)),       # z 1024
+    (synth.BC_WIRE, (16, 32, 128), (0.8, 0.4, 0.3)),        # y 64 (zero padded), z 128 (periodic)
     # x passes (row pairs; odd row counts leave a last pair with one row)
     (synth.BC_PERIODIC, (64, 6, 6), (0.3, 0.5, 0.6)),       # x 64
     (synth.BC_FREE, (32, 5, 9), (0.4, 2.56, 1.42)),         # x 64 (zero padded), 45 rows
@@ -180,6 +183,30 @@ def _solve_pair(gps, ctx, p, kind="gpe", tol_rel=1e-13, **okw):
         lam = oracle.pb.linear_lambda(gam, p.electrolyte)
         ref, info = oracle.solve_lpb(g, p.rho, p.eps, lam, tol_abs=0.0, tol_rel=tol_rel, max_iter=2000)
     return N(phi, g.shape), ref, rep, info
+
+
+def _wire_chain(n=32, nz=48):
+    return synth.wire_chain(n=n, nz=nz)
+
+
+@pytest.mark.parametrize("kind", ["gpe", "lpb"])
+def test_wire_solves(gps, ctx, kind):
+    p = _wire_chain()
+    got, ref, rep, info = _solve_pair(gps, ctx, p, kind=kind)
+    assert rep.status == 0
+    assert abs(rep.iters - info["iters"]) <= 2
+    assert rel2(got, ref) <= 1e-10
+
+
+def test_wire_nlpb(gps, ctx):
+    p = _wire_chain(n=24, nz=32)
+    el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.pb_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), el, "nlpb", phi,
+                       gps.default_opts(tol_outer=1e-11, max_iter=3000))
+    ref, info = oracle.solve_nlpb(p.grid, p.rho, p.eps, p.electrolyte, p.eps0, tol=1e-11, max_iter=3000)
+    assert info["converged"] and rep.status == 0
+    assert rel2(N(phi, p.grid.shape), ref) <= 1e-9
 
 
 def test_gpe_free_single_cavity(gps, ctx):

@@ -59,7 +59,17 @@ CASES = {
     "free_ragged": lambda: _ragged_free(),
     "periodic": lambda: _neutral(synth.workload(2, n=32, count=4)),
     "surface": lambda: synth.workload(3, nxy=24, nz=96, count=4),
+    "wire": lambda: _wire(),
 }
+
+
+def _wire():
+    """Wire BC (periodic z, free x and y): two cavities along z."""
+    g = synth.Grid(24, 24, 32, 0.4, 0.4, 0.35, synth.BC_WIRE)
+    c = 12 * 0.4
+    eps = synth.rigid_cavity(g, [(2.2, (c, c, 2.8)), (2.2, (c, c, 8.4))], 0.5)
+    rho = synth.gaussian_charges(g, [(1.0, 0.9, (c - 0.5, c, 2.8)), (-1.0, 0.8, (c + 0.5, c, 8.4))])
+    return synth.Problem("wire", g, rho, eps)
 
 
 def _neutral(p):
