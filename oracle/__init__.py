@@ -18,7 +18,8 @@ Modules
   pb         ionic charge (Eq. rhoions, ionsconcPB) and Algorithms 3 and 4
   dense      dense assembly of the discrete operator, direct and Newton solves
   sc         Algorithm 1 (SC) and PSD / PSD+DIIS comparison solvers (Eqs. remap, rhoiter, PrePSD)
+  dft        sccs dielectric, polarization charge, v_eps, electrostatic energy (Eqs. sccs, rhopol, veps)
 """
-from . import constants, fd16, green, operators, pcg, pb, dense, sc  # noqa: F401
+from . import constants, fd16, green, operators, pcg, pb, dense, sc, dft  # noqa: F401
 from .pcg import solve_gpe, solve_lpb  # noqa: F401
 from .pb import solve_nlpb  # noqa: F401
