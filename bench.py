@@ -235,6 +235,7 @@ def run_ours(args, ws, rank, local):
     nonlinear = None if args.no_nonlinear else run_nonlinear(gps, local, flush)
     comparison = None if args.no_comparison else run_comparison(gps, local, flush)
     wire = None if args.no_wire else run_wire(gps, local, flush)
+    dft = None if args.no_dft else run_dft(gps, local, flush)
     serving = None if args.no_serving else run_serving(gps, local, args)
 
     # roofline of the dominant kernel (largest share of kernel time in warm-up)
@@ -262,6 +263,7 @@ def run_ours(args, ws, rank, local):
         "nonlinear": nonlinear,
         "comparison": comparison,
         "wire": wire,
+        "dft": dft,
         "serving": serving,
         "roofline": roof,
         "gpu_launches": int(launches),
@@ -464,6 +466,52 @@ def run_wire(gps, device, flush):
                      "certificate": rep.fixed_point_res}
     ctx.close()
     return out
+
+
+def run_dft(gps, device, flush):
+    """DFT-facing passes on the 128^3 periodic workload's GPU potential: the
+    sccs dielectric of a synthetic electron density (a Gaussian of peak 0.2
+    and width 1.2 bohr on every solute charge, spanning the sccs transition
+    rho_max = 5e-3, rho_min = 1e-4), the polarization charge, v_eps and the
+    electrostatic energy; CUDA-event time per call (mean of 5 after one
+    warm-up), L2 flushed before each."""
+    import torch
+    import synth
+    p = synth.workload(2)
+    g = gps.grid_from(p.grid)
+    rho = torch.from_numpy(p.rho.ravel()).to(device)
+    eps = torch.from_numpy(p.eps.ravel()).to(device)
+    norm = 0.2 * (2 * np.pi * 1.2 ** 2) ** 1.5
+    rho_e_h = synth.gaussian_charges(p.grid, [(norm, 1.2, c) for _, _, c in p.charges])
+    rho_e = torch.from_numpy(rho_e_h.ravel()).to(device)
+    ctx = gps.Context(device)
+    phi = torch.zeros_like(rho)
+    ctx.gpe_solve(g, rho, eps, phi, gps.default_opts(tol_abs=1e-10))
+    e_s, d_s, out = torch.empty_like(rho), torch.empty_like(rho), torch.empty_like(rho)
+    stream = torch.cuda.current_stream()
+    calls = {"sccs_eps": lambda: ctx.sccs_eps(rho_e, e_s, d_s),
+             "polarization_charge": lambda: ctx.polarization_charge(g, rho, eps, phi, out),
+             "v_eps": lambda: ctx.v_eps(g, d_s, phi, out),
+             "electrostatic_energy": lambda: ctx.electrostatic_energy(g, rho, eps, phi)}
+    res = {"workload": p.name, "npts": p.grid.npts}
+    for name, fn in calls.items():
+        fn()
+        ts = []
+        for _ in range(5):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.mean(ts))
+        res[name] = {"ms": ms, "grid_pts_per_s": p.grid.npts / (ms / 1e3)}
+    res["transition_fraction"] = float(((rho_e_h > 1e-4) & (rho_e_h < 5e-3)).mean())
+    e1_, e2_ = ctx.electrostatic_energy(g, rho, eps, phi)
+    res["energy"] = {"rho_phi": e1_, "eps_grad2": e2_}
+    ctx.close()
+    return res
 
 
 def run_serving(gps, device, args, count=None):
@@ -741,6 +789,7 @@ def main():
     ap.add_argument("--no-nonlinear", action="store_true")
     ap.add_argument("--no-comparison", action="store_true")
     ap.add_argument("--no-wire", action="store_true")
+    ap.add_argument("--no-dft", action="store_true")
     ap.add_argument("--clocks-log", default=None, help="keep the nvidia-smi samples of the timed region here")
     ap.add_argument("--serving-count", type=int, default=24)
     ap.add_argument("--passes", default=None, choices=sorted(PASS_CASES),

@@ -245,10 +245,51 @@ int gps_precondition(gps_ctx* ctx, const gps_grid* grid, const double* s_dev,
 
 /* Ionic charge of Eqs. (rhoions, ionsconcPB) with the cavity exclusion
  * function: out = gamma sum_i z_i n_i exp(-z_i phi / kT), exponent capped at
- * +40.  Inputs phi_dev, eps_dev; output out_dev. */
+ * +40; with el->packing > 0 the steric distribution of Eq. (ionsconcMPB)
+ * (see gps_electrolyte).  Inputs phi_dev, eps_dev; output out_dev. */
 int gps_ionic_charge(gps_ctx* ctx, const gps_grid* grid, const double* phi_dev,
                      const double* eps_dev, const gps_electrolyte* el,
                      double* out_dev, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Quantities a DFT code takes from the solve (Sec. "Charge-dependent
+ * cavity").  Gradients by the order-16 central differences (periodic axes
+ * wrap and need at least 8 points; free faces continue the field by its face
+ * value).  All arrays are nx*ny*nz doubles on the current device unless
+ * stated; the calls are asynchronous on the stream except
+ * gps_electrostatic_energy, which returns after synchronizing it. */
+
+/* Charge-dependent (sccs) dielectric, Eq. (sccs): eps = 1 where rho_elec >=
+ * rho_max, eps0 where rho_elec <= rho_min, and eps0^w(rho) in between, w =
+ * (z - sin z) / (2 pi), z = 2 pi ln(rho_max / rho) / ln(rho_max / rho_min).
+ * (The printed middle branch eps0 exp(w) is 1 at neither threshold; eps0^w
+ * is continuous with both.)  deps_dev (may be NULL) receives d eps / d rho_elec
+ * (0 outside the transition).  n values; rho_max > rho_min > 0, eps0 > 1.
+ * The paper uses rho_max = 5e-3, rho_min = 1e-4. */
+int gps_sccs_eps(gps_ctx* ctx, size_t n, const double* rho_elec_dev, double rho_max, double rho_min,
+                 double eps0, double* eps_dev, double* deps_dev, void* cuda_stream);
+
+/* Polarization charge, Eqs. (remap, rhopol): rho_pol = grad ln eps . grad phi
+ * / 4 pi - ((eps - 1) / eps) rho (the sign Eq. remap requires; the paper
+ * prints "+").  eps > 0. */
+int gps_polarization_charge(gps_ctx* ctx, const gps_grid* grid, const double* rho_dev,
+                            const double* eps_dev, const double* phi_dev, double* rho_pol_dev,
+                            void* cuda_stream);
+
+/* Kohn-Sham correction of a charge-dependent cavity, Eq. (veps):
+ * v_eps = -(1/8 pi) (d eps / d rho_elec) |grad phi|^2. */
+int gps_v_eps(gps_ctx* ctx, const gps_grid* grid, const double* deps_dev, const double* phi_dev,
+              double* v_eps_dev, void* cuda_stream);
+
+/* Electrostatic energy in its two forms (Sec. "Charge-dependent cavity"):
+ * e_rho_phi = (1/2) sum rho phi h^3 and e_eps_grad = (1/8 pi) sum eps
+ * |grad phi|^2 h^3.  They are equal up to discretization error for a converged
+ * phi whose field is contained in the box; for a charged solute with free BC
+ * the second misses the field energy outside the box.  Either output pointer
+ * may be NULL. */
+int gps_electrostatic_energy(gps_ctx* ctx, const gps_grid* grid, const double* rho_dev,
+                             const double* eps_dev, const double* phi_dev, double* e_rho_phi,
+                             double* e_eps_grad, void* cuda_stream);
 
 /* ------------------------------------------------------------------------
  * Batched and served solves.  A request carries its own grid, problem,

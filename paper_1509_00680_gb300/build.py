@@ -14,8 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgps.so")
-SOURCES = ["fft.cu", "fft_col.cu", "kernels.cu", "sc.cu", "api.cu", "noalloc.cu"]
-HEADERS = ["gps_internal.h", "device_util.cuh", "kernels.h", "fft_common.cuh"]
+SOURCES = ["fft.cu", "fft_col.cu", "kernels.cu", "sc.cu", "dft.cu", "api.cu", "noalloc.cu"]
+HEADERS = ["gps_internal.h", "device_util.cuh", "kernels.h", "fft_common.cuh", "stencil16.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

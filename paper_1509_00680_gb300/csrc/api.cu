@@ -125,6 +125,22 @@ void fd16_first_coeffs(double* d) {
   }
 }
 
+// Order-16 first-derivative stencil of a grid: wrapping axes per BC.
+Stencil16 stencil16_of(const gps_grid& g) {
+  Stencil16 s{};
+  s.nx = g.nx;
+  s.ny = g.ny;
+  s.nz = g.nz;
+  s.perx = g.bc == GPS_BC_PERIODIC || g.bc == GPS_BC_SURFACE;
+  s.pery = s.perx;
+  s.perz = g.bc == GPS_BC_PERIODIC || g.bc == GPS_BC_WIRE;
+  s.ihx = 1.0 / g.hx;
+  s.ihy = 1.0 / g.hy;
+  s.ihz = 1.0 / g.hz;
+  fd16_first_coeffs(s.d);
+  return s;
+}
+
 // Even (cosine) transform matrix C[k][j] = w_j cos(2 pi j k / M) * scale,
 // j = 0..M/2, k = 0..K-1, w_0 = w_(M/2) = 1, otherwise 2.
 std::vector<double> cosine_matrix(int M, int K, double scale) {
@@ -603,6 +619,7 @@ struct Pool {
   int ws_kind = -1;
   gps_electrolyte ws_el{};
   ScWork sc;
+  double *dft_tmp = nullptr, *dft_part = nullptr;   // DFT-facing passes: scratch, partial sums
   DevMem mem;
 
   ~Pool() {
@@ -1421,19 +1438,10 @@ int solve_comparison(Pool& P, const double* rho, const double* eps, double* phi,
   a.hist_mr = w.small;
   a.diis_B = w.small + 16;
   a.diis_c = w.small + 16 + kMaxDiis * kMaxDiis;
-  a.nx = g.nx;
-  a.ny = g.ny;
-  a.nz = g.nz;
-  a.perx = g.bc == GPS_BC_PERIODIC || g.bc == GPS_BC_SURFACE;
-  a.pery = a.perx;
-  a.perz = g.bc == GPS_BC_PERIODIC || g.bc == GPS_BC_WIRE;
-  a.ihx = 1.0 / g.hx;
-  a.ihy = 1.0 / g.hy;
-  a.ihz = 1.0 / g.hz;
+  a.s16 = stencil16_of(g);
   a.n = n;
   a.periodic = g.bc == GPS_BC_PERIODIC;
   a.inv_n = 1.0 / (double)n;
-  fd16_first_coeffs(a.d);
   a.alpha = o.alpha;
 
   SlotState s{};
@@ -1856,6 +1864,83 @@ int gps_ionic_charge(gps_ctx* ctx, const gps_grid* grid, const double* phi, cons
   const bool steric = el->packing > 0;
   if (steric && validate_steric(el) != GPS_OK) return GPS_ERR_INVALID;
   launch_ionic_charge(phi, eps, out, n, ion_params(el, steric), st);
+  return finish(GPS_OK, st);
+  GPS_GUARD_END
+}
+
+// grids of the stencil passes: validate_grid, and periodic axes >= 8 points
+int validate_stencil_grid(const gps_grid* g) {
+  const int v = validate_grid(g);
+  if (v != GPS_OK) return v;
+  const Stencil16 s = stencil16_of(*g);
+  if ((s.perx && g->nx < 8) || (s.pery && g->ny < 8) || (s.perz && g->nz < 8)) return GPS_ERR_INVALID;
+  return GPS_OK;
+}
+
+int gps_sccs_eps(gps_ctx* ctx, size_t n, const double* rho_elec, double rho_max, double rho_min, double eps0,
+                 double* eps, double* deps, void* stream) {
+  if (!ctx || !rho_elec || !eps || n == 0) return GPS_ERR_INVALID;
+  if (!(rho_min > 0.0 && rho_max > rho_min && eps0 > 1.0)) return GPS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  GPS_GUARD_BEGIN
+  cudaSetDevice(ctx->device);
+  launch_sccs(rho_elec, eps, deps, n, rho_max, rho_min, eps0, st);
+  return finish(GPS_OK, st);
+  GPS_GUARD_END
+}
+
+int gps_polarization_charge(gps_ctx* ctx, const gps_grid* grid, const double* rho, const double* eps,
+                            const double* phi, double* out, void* stream) {
+  if (!ctx || !grid || !rho || !eps || !phi || !out) return GPS_ERR_INVALID;
+  int v = validate_stencil_grid(grid);
+  if (v != GPS_OK) return v;
+  cudaStream_t st = (cudaStream_t)stream;
+  GPS_GUARD_BEGIN
+  cudaSetDevice(ctx->device);
+  Pool* P = direct_pool(ctx, grid, st);
+  if (!P->dft_tmp) P->dft_tmp = P->mem.alloc<double>(P->n);
+  launch_polarization(stencil16_of(*grid), rho, eps, phi, P->dft_tmp, out, P->n, st);
+  return finish(GPS_OK, st);
+  GPS_GUARD_END
+}
+
+int gps_v_eps(gps_ctx* ctx, const gps_grid* grid, const double* deps, const double* phi, double* out,
+              void* stream) {
+  if (!ctx || !grid || !deps || !phi || !out) return GPS_ERR_INVALID;
+  int v = validate_stencil_grid(grid);
+  if (v != GPS_OK) return v;
+  cudaStream_t st = (cudaStream_t)stream;
+  GPS_GUARD_BEGIN
+  cudaSetDevice(ctx->device);
+  const size_t n = (size_t)grid->nx * grid->ny * grid->nz;
+  launch_veps(stencil16_of(*grid), deps, phi, out, n, st);
+  return finish(GPS_OK, st);
+  GPS_GUARD_END
+}
+
+int gps_electrostatic_energy(gps_ctx* ctx, const gps_grid* grid, const double* rho, const double* eps,
+                             const double* phi, double* e_rho_phi, double* e_eps_grad, void* stream) {
+  if (!ctx || !grid || !rho || !eps || !phi) return GPS_ERR_INVALID;
+  int v = validate_stencil_grid(grid);
+  if (v != GPS_OK) return v;
+  cudaStream_t st = (cudaStream_t)stream;
+  GPS_GUARD_BEGIN
+  cudaSetDevice(ctx->device);
+  Pool* P = direct_pool(ctx, grid, st);
+  const int nb = dft_blocks(P->n);
+  if (!P->dft_part) P->dft_part = P->mem.alloc<double>(2 * (size_t)nb);
+  launch_energy(stencil16_of(*grid), rho, eps, phi, P->n, P->dft_part, st);
+  std::vector<double> part(2 * (size_t)nb);
+  ck(cudaMemcpyAsync(part.data(), P->dft_part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  ck(cudaStreamSynchronize(st));
+  double a = 0.0, b = 0.0;   // fixed order: the same bits on every call
+  for (int i = 0; i < nb; ++i) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
+  }
+  const double dv = grid->hx * grid->hy * grid->hz;
+  if (e_rho_phi) *e_rho_phi = 0.5 * a * dv;
+  if (e_eps_grad) *e_eps_grad = b * dv / (8.0 * kPi);
   return finish(GPS_OK, st);
   GPS_GUARD_END
 }

@@ -5,6 +5,7 @@
 #include <stddef.h>
 
 #include "gps_internal.h"
+#include "stencil16.cuh"
 
 namespace gps {
 
@@ -60,6 +61,19 @@ void launch_wire_ghat(double* out, int mx, int my, int mz, double dkx, double dk
 void launch_axis_matrix(const double* in, double* out, const double* C, int A, int J, int B, int K,
                         cudaStream_t st);
 
+// ---- DFT-facing quantities (dft.cu) --------------------------------------
+
+int dft_blocks(size_t n);
+void launch_sccs(const double* rho, double* eps, double* deps, size_t n, double rho_max, double rho_min,
+                 double eps0, cudaStream_t st);
+// rho_pol; tmp: n doubles of scratch (ln eps)
+void launch_polarization(const Stencil16& s, const double* rho, const double* eps, const double* phi,
+                         double* tmp, double* out, size_t n, cudaStream_t st);
+void launch_veps(const Stencil16& s, const double* deps, const double* phi, double* out, size_t n, cudaStream_t st);
+// part: 2 x dft_blocks(n) doubles, per block sum rho phi and sum eps |grad phi|^2
+void launch_energy(const Stencil16& s, const double* rho, const double* eps, const double* phi, size_t n,
+                   double* part, cudaStream_t st);
+
 // ---- comparison solvers (sc.cu): Algorithm 1 (SC), PSD, PSD + DIIS ------
 
 constexpr int kMaxDiis = 8;   // GPS_MAX_DIIS
@@ -89,12 +103,10 @@ struct ScArgs {
   double* diis_B;               // kMaxDiis x kMaxDiis Gram matrix (ring-slot indexed)
   double* diis_c;               // coefficients of the current combination
   int hist_m;
-  int nx, ny, nz, perx, pery, perz;
-  double ihx, ihy, ihz;         // 1 / h
+  Stencil16 s16;                // grid, wrapping axes, order-16 coefficients
   size_t n;
   int periodic;
   double inv_n;
-  double d[9];                  // order-16 first-derivative coefficients d_1..d_8
   double alpha;                 // PSD: fixed step, 0 = steepest descent
   int* acted;                   // optional: set by a launch that did work (profiling)
 };

@@ -54,34 +54,12 @@ __device__ __forceinline__ double g_dot_grad(const double* __restrict__ u, size_
                                              const ScArgs& a) {
   const double gx = a.gx[idx], gy = a.gy[idx], gz = a.gz[idx];
   if (gx == 0.0 && gy == 0.0 && gz == 0.0) return 0.0;
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const double* row = u + (idx - i);
-  const size_t sy = nx, sz = (size_t)nx * ny;
-  const size_t bxz = (size_t)k * sz + i, bxy = (size_t)j * nx + i;
-  double dx = 0.0, dy = 0.0, dz = 0.0;
-#pragma unroll
-  for (int m = 1; m <= 8; ++m) {
-    int ip = i + m, im = i - m;
-    if (a.perx) { ip = ip >= nx ? ip - nx : ip; im = im < 0 ? im + nx : im; }
-    else { ip = ip >= nx ? nx - 1 : ip; im = im < 0 ? 0 : im; }
-    int jp = j + m, jm = j - m;
-    if (a.pery) { jp = jp >= ny ? jp - ny : jp; jm = jm < 0 ? jm + ny : jm; }
-    else { jp = jp >= ny ? ny - 1 : jp; jm = jm < 0 ? 0 : jm; }
-    int kp = k + m, km = k - m;
-    if (a.perz) { kp = kp >= nz ? kp - nz : kp; km = km < 0 ? km + nz : km; }
-    else { kp = kp >= nz ? nz - 1 : kp; km = km < 0 ? 0 : km; }
-    const double d = a.d[m];
-    dx = fma(d, row[ip] - row[im], dx);
-    dy = fma(d, u[bxz + (size_t)jp * sy] - u[bxz + (size_t)jm * sy], dy);
-    dz = fma(d, u[bxy + (size_t)kp * sz] - u[bxy + (size_t)km * sz], dz);
-  }
-  return gx * dx * a.ihx + gy * dy * a.ihy + gz * dz * a.ihz;
+  const double3 gu = grad16(u, idx, i, j, k, a.s16);
+  return gx * gu.x + gy * gu.y + gz * gu.z;
 }
 
 __device__ __forceinline__ void point_of(size_t idx, const ScArgs& a, int* i, int* j, int* k) {
-  *i = (int)(idx % a.nx);
-  *j = (int)((idx / a.nx) % a.ny);
-  *k = (int)(idx / ((size_t)a.nx * a.ny));
+  point_of16(idx, a.s16, i, j, k);
 }
 
 // Whether the solve is still iterating; marks the launch as having done work.
@@ -158,33 +136,13 @@ __global__ void k_sc_prep(ScArgs a, int psd, double* __restrict__ phi0, double* 
 
 // g = grad(tmp) by order-16 central differences (tmp = ln eps).
 __global__ void k_sc_grad(ScArgs a) {
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
   SC_STRIDE(idx, a.n) {
     int i, j, k;
     point_of(idx, a, &i, &j, &k);
-    const double* row = a.tmp + (idx - i);
-    const size_t sy = nx, sz = (size_t)nx * ny;
-    const size_t bxz = (size_t)k * sz + i, bxy = (size_t)j * nx + i;
-    double dx = 0.0, dy = 0.0, dz = 0.0;
-#pragma unroll
-    for (int m = 1; m <= 8; ++m) {
-      int ip = i + m, im = i - m;
-      if (a.perx) { ip = ip >= nx ? ip - nx : ip; im = im < 0 ? im + nx : im; }
-      else { ip = ip >= nx ? nx - 1 : ip; im = im < 0 ? 0 : im; }
-      int jp = j + m, jm = j - m;
-      if (a.pery) { jp = jp >= ny ? jp - ny : jp; jm = jm < 0 ? jm + ny : jm; }
-      else { jp = jp >= ny ? ny - 1 : jp; jm = jm < 0 ? 0 : jm; }
-      int kp = k + m, km = k - m;
-      if (a.perz) { kp = kp >= nz ? kp - nz : kp; km = km < 0 ? km + nz : km; }
-      else { kp = kp >= nz ? nz - 1 : kp; km = km < 0 ? 0 : km; }
-      const double d = a.d[m];
-      dx = fma(d, row[ip] - row[im], dx);
-      dy = fma(d, a.tmp[bxz + (size_t)jp * sy] - a.tmp[bxz + (size_t)jm * sy], dy);
-      dz = fma(d, a.tmp[bxy + (size_t)kp * sz] - a.tmp[bxy + (size_t)km * sz], dz);
-    }
-    a.gx[idx] = dx * a.ihx;
-    a.gy[idx] = dy * a.ihy;
-    a.gz[idx] = dz * a.ihz;
+    const double3 g = grad16(a.tmp, idx, i, j, k, a.s16);
+    a.gx[idx] = g.x;
+    a.gy[idx] = g.y;
+    a.gz[idx] = g.z;
   }
 }
 

@@ -89,6 +89,13 @@ _SIGS = {
     "gps_ionic_charge": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P,
                                         ctypes.POINTER(gps_electrolyte), _P, _P]),
     "gps_vacuum_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(gps_grid), _P, _P, _P]),
+    "gps_sccs_eps": (ctypes.c_int, [_P, ctypes.c_size_t, _P, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, _P, _P, _P]),
+    "gps_polarization_charge": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P, _P, _P]),
+    "gps_v_eps": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P, _P]),
+    "gps_electrostatic_energy": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P,
+                                                ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_double), _P]),
     "gps_batch_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(gps_request),
                                        ctypes.POINTER(gps_report)]),
     "gps_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_size_t, ctypes.c_int]),
@@ -285,6 +292,29 @@ class Context:
         _check(load().gps_ionic_charge(self.handle, ctypes.byref(grid), _dev(phi), _dev(eps),
                                        ctypes.byref(electrolyte), _dev(out), _stream(stream)),
                "gps_ionic_charge")
+
+    # --- DFT-facing quantities ------------------------------------------
+    def sccs_eps(self, rho_elec, eps, deps=None, rho_max=5e-3, rho_min=1e-4, eps0=78.36, stream=None):
+        _check(load().gps_sccs_eps(self.handle, rho_elec.numel(), _dev(rho_elec), rho_max, rho_min, eps0,
+                                   _dev(eps), _dev(deps) if deps is not None else None, _stream(stream)),
+               "gps_sccs_eps")
+
+    def polarization_charge(self, grid, rho, eps, phi, out, stream=None):
+        _check(load().gps_polarization_charge(self.handle, ctypes.byref(grid), _dev(rho), _dev(eps),
+                                              _dev(phi), _dev(out), _stream(stream)),
+               "gps_polarization_charge")
+
+    def v_eps(self, grid, deps, phi, out, stream=None):
+        _check(load().gps_v_eps(self.handle, ctypes.byref(grid), _dev(deps), _dev(phi), _dev(out),
+                                _stream(stream)), "gps_v_eps")
+
+    def electrostatic_energy(self, grid, rho, eps, phi, stream=None):
+        """(1/2 sum rho phi h^3, 1/(8 pi) sum eps |grad phi|^2 h^3)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(load().gps_electrostatic_energy(self.handle, ctypes.byref(grid), _dev(rho), _dev(eps),
+                                               _dev(phi), ctypes.byref(a), ctypes.byref(b),
+                                               _stream(stream)), "gps_electrostatic_energy")
+        return a.value, b.value
 
 
 def make_request(grid, kind, rho, eps, phi, electrolyte=None, opts=None):
