@@ -135,7 +135,8 @@ typedef struct {
   double tol_outer;      /* NLPB outer tolerance on the ionic-charge residual */
   double eta;            /* mixing: NLPB printed Algorithm 4; GPS_SC rho_iter (Algorithm 1) */
   int outer_mode;        /* gps_outer_mode */
-  double forcing;        /* NLPB Newton: relative inner tolerance cap (e.g. 1e-2) */
+  double forcing;        /* NLPB Newton: cap of the inner solve's relative tolerance, which is
+                            min(forcing, F/F_0) (F the outer residual); in (0, 1) */
   int precision;         /* gps_precision */
   double mixed_switch;   /* GPS_MIXED: FP64 preconditioner until ||r|| <= mixed_switch*||r_0|| */
   int certify;           /* 1: compute rep->fixed_point_res (always done for GPS_MIXED) */
@@ -173,7 +174,7 @@ typedef struct {
 typedef struct gps_ctx gps_ctx;
 
 /* Fill *opts with defaults: tol_abs 1e-10, tol_rel 0, max_iter 500,
- * max_outer 100, tol_outer 1e-10, eta 0.6, Newton outer mode, forcing 1e-2,
+ * max_outer 100, tol_outer 1e-10, eta 0.6, Newton outer mode, forcing 0.3,
  * FP64, mixed_switch 1e-2, certify 0, warm_start 0, method GPS_PCG (alpha 0,
  * diis 0). */
 void gps_default_opts(gps_opts* opts);
