@@ -381,6 +381,15 @@ int gps_vacuum_solve_noalloc(const gps_grid* grid, const double* sigma_dev, doub
 int gps_set_profiling(gps_ctx* ctx, int mask);
 int gps_get_profile(gps_ctx* ctx, long long* launches, double* total_ms, int reset);
 
+/* Radix order of the shared-memory FFT passes.  -1 (the default): the tuner
+ * times, per grid and spectrum precision, the orders 0 (radix-8 stages first),
+ * 1 (radix-8 stages last), 2 (radix 4) and, for the FP64 spectrum, 3 (radix
+ * 16 first) and keeps the fastest; 0..3: plans made from now on use that
+ * order where it applies to the length (else order 0), for reproducible
+ * plans and for tests of each order.  Clears the process-wide tuning cache;
+ * shapes already planned in a context keep their plans (use a new context). */
+int gps_set_radix_order(int order);
+
 /* Number of CUDA kernels this library has launched in the process so far. */
 unsigned long long gps_kernel_launches(void);
 

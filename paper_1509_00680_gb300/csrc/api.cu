@@ -66,7 +66,13 @@ bool make_sched(int L, FftSched* s, int order = 0) {
   int p2 = 0;
   while (rem % 2 == 0) { rem /= 2; ++p2; }
   std::vector<int> twos;
-  if (order == 2) {
+  if (order == 3) {   // radix 16 first (FP64 kernels only); no 16 in L: not a new schedule
+    if (p2 < 4) return false;
+    while (p2 >= 4) { twos.push_back(16); p2 -= 4; }
+    if (p2 == 3) twos.push_back(8);
+    if (p2 == 2) twos.push_back(4);
+    if (p2 == 1) twos.push_back(2);
+  } else if (order == 2) {
     while (p2 >= 2) { twos.push_back(4); p2 -= 2; }
     if (p2) twos.push_back(2);
   } else {
@@ -764,6 +770,7 @@ struct TuneVal {
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune;
+int g_radix_order = -1;   // gps_set_radix_order: -1 tunes the radix order, else this one
 
 template <typename F>
 float time_launch(F&& launch, cudaStream_t st) {
@@ -810,6 +817,16 @@ std::vector<int> batch_candidates(int b0, int L, size_t vbytes, bool fixed) {
     if (x_lines_smem_bytes(L, b, vbytes) <= 220 * 1024) c.push_back(b);
   if (c.empty()) c.push_back(1);
   return c;
+}
+
+// The radix orders the tuner may try for a transform of length L: all of
+// them, or the one gps_set_radix_order chose (order 0 where that one does
+// not apply to L).
+bool order_allowed(int L, int order, int norders) {
+  if (g_radix_order < 0) return true;
+  FftSched tmp;
+  const bool applies = g_radix_order < norders && make_sched(L, &tmp, g_radix_order);
+  return order == (applies ? g_radix_order : 0);
 }
 
 template <typename V>
@@ -860,10 +877,13 @@ void tune_spec(Shape& S, cudaStream_t st) {
     const bool fixx = std::is_same<V, dfc>::value && col_pass_supported(S.Px);
     const bool fixy = !f64 && col_pass_supported(S.Py);
     const bool fixz = !f64 && col_pass_supported(S.Pz);
+    // radix orders: 8s first, 8s last, 4s, and for FP64 16s first
+    const int norders = f64 ? 4 : 3;
     // x passes: lines per CTA and radix order of Px
     float tbest = 1e30f;
     for (int lines : batch_candidates(S.g.lines_x, S.Px, sizeof(V), fixx))
-      for (int order = 0; order < (fixx ? 1 : 3); ++order) {
+      for (int order = 0; order < (fixx ? 1 : norders); ++order) {
+        if (!fixx && !order_allowed(S.Px, order, norders)) continue;
         PassGeom g = best.g;
         g.lines_x = lines;
         FftSched fx;
@@ -874,7 +894,8 @@ void tune_spec(Shape& S, cudaStream_t st) {
       }
     tbest = 1e30f;
     for (int tile : batch_candidates(S.g.tile_y, S.Py, sizeof(V), fixy))
-      for (int order = 0; order < (fixy ? 1 : 3); ++order) {
+      for (int order = 0; order < (fixy ? 1 : norders); ++order) {
+        if (!fixy && !order_allowed(S.Py, order, norders)) continue;
         PassGeom g = best.g;
         g.tile_y = tile;
         FftSched fy;
@@ -885,7 +906,8 @@ void tune_spec(Shape& S, cudaStream_t st) {
       }
     tbest = 1e30f;
     for (int tile : batch_candidates(S.g.tile_z, S.Pz, sizeof(V), fixz))
-      for (int order = 0; order < (fixz ? 1 : 3); ++order) {
+      for (int order = 0; order < (fixz ? 1 : norders); ++order) {
+        if (!fixz && !order_allowed(S.Pz, order, norders)) continue;
         PassGeom g = best.g;
         g.tile_z = tile;
         FftSched fz;
@@ -2048,6 +2070,14 @@ void gps_server_destroy(gps_server* s) {
   cudaSetDevice(s->eng.device);
   cudaDeviceSynchronize();
   delete s;
+}
+
+int gps_set_radix_order(int order) {
+  if (order < -1 || order > 3) return GPS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_radix_order = order;
+  g_tune.clear();
+  return GPS_OK;
 }
 
 int gps_set_profiling(gps_ctx* ctx, int mask) {

@@ -83,7 +83,10 @@ __device__ __forceinline__ void stage_any(const V* in, V* out, int L, int Ns, in
 
 // Full 1D transform of a batch of lines held in a; b is the ping-pong partner.
 // Returns the buffer holding the result.  Ends with a __syncthreads().
-template <typename V, int DIR>
+// MR: the largest radix the kernel is built for (16 only in the FP64 kernels
+// launched for schedules that contain a radix-16 stage, so that the other
+// kernels keep their register budget).
+template <typename V, int DIR, int MR = 8>
 __device__ __forceinline__ V* fft_lines(V* a, V* b, const FftSched& s, int ls, int nlines, const V* tw) {
   V* in = a;
   V* out = b;
@@ -94,6 +97,9 @@ __device__ __forceinline__ V* fft_lines(V* a, V* b, const FftSched& s, int ls, i
       case 3: stage_any<V, DIR, 3>(in, out, s.L, Ns, ls, nlines, tw); break;
       case 4: stage_any<V, DIR, 4>(in, out, s.L, Ns, ls, nlines, tw); break;
       case 5: stage_any<V, DIR, 5>(in, out, s.L, Ns, ls, nlines, tw); break;
+      case 16:
+        if constexpr (MR == 16) stage_any<V, DIR, 16>(in, out, s.L, Ns, ls, nlines, tw);
+        break;
       default: stage_any<V, DIR, 8>(in, out, s.L, Ns, ls, nlines, tw); break;
     }
     __syncthreads();
@@ -162,7 +168,7 @@ __device__ __forceinline__ void pair_offsets(const PassGeom& g, int p0, int nl, 
   }
 }
 
-template <typename V>
+template <typename V, int MR>
 __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, const V* __restrict__ twg,
                                                    Batch b, PipeArgs a) {
   using T = typename Real<V>::T;
@@ -214,7 +220,7 @@ __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, cons
     }
   }
   __syncthreads();
-  const V* res = fft_lines<V, -1>(b0, b1, s, ls, nl, tw);
+  const V* res = fft_lines<V, -1, MR>(b0, b1, s, ls, nl, tw);
   const T half = T(0.5);
   for (LineIter it(g.Hx); it.l < nl; it.next()) {
     const int l = it.l, k = it.j;
@@ -229,7 +235,7 @@ __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, cons
     grid_reduce(sum, b.partials + (size_t)slot * b.pstride, &b.st[slot].counter[CNT_MU], &b.st[slot].mu_sum);
 }
 
-template <typename V, int DIR>
+template <typename V, int DIR, int MR>
 __global__ void __launch_bounds__(kThreads) k_y(PassGeom g, FftSched s, const V* __restrict__ twg,
                                                Batch b, PipeArgs a) {
   const int slot = pass_slot<V>(b);
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_y(PassGeom g, FftSched s, const V*
   V* col = W + plane + kx0 + c;
   if (act) load_column<V>(b0 + c * ls, col, g.Hx, y0, ystep, L, nload);
   __syncthreads();
-  const V* res = fft_lines<V, DIR>(b0, b1, s, ls, nl, tw);
+  const V* res = fft_lines<V, DIR, MR>(b0, b1, s, ls, nl, tw);
   const int nstore = DIR < 0 ? L : g.ny;  // inverse: crop to y < ny
   if (act) {
     const V* line = res + c * ls;
@@ -260,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) k_y(PassGeom g, FftSched s, const V*
   }
 }
 
-template <typename V>
+template <typename V, int MR>
 __global__ void __launch_bounds__(kThreads) k_z(PassGeom g, FftSched s, const V* __restrict__ twg,
                                                Batch b, PipeArgs a) {
   using T = typename Real<V>::T;
@@ -286,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) k_z(PassGeom g, FftSched s, const V*
   V* col = W + colbase + c;
   if (act) load_column<V>(b0 + c * ls, col, zstride, z0, zstep, L, g.nz);
   __syncthreads();
-  V* res = fft_lines<V, -1>(b0, b1, s, ls, nl, tw);
+  V* res = fft_lines<V, -1, MR>(b0, b1, s, ls, nl, tw);
   V* other = (res == b0) ? b1 : b0;
   const int kyp = min(ky, g.Py - ky);
   const int hy = g.Py / 2 + 1;
@@ -333,14 +339,14 @@ __global__ void __launch_bounds__(kThreads) k_z(PassGeom g, FftSched s, const V*
     }
   }
   __syncthreads();
-  const V* fin = fft_lines<V, +1>(res, other, s, ls, nl, tw);
+  const V* fin = fft_lines<V, +1, MR>(res, other, s, ls, nl, tw);
   if (act) {
     const V* line = fin + c * ls;
     for (int z = z0; z < g.nz; z += zstep) col[(size_t)z * zstride] = line[pidx<V>(z)];
   }
 }
 
-template <typename V>
+template <typename V, int MR>
 __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, const V* __restrict__ twg,
                                                    Batch b, PipeArgs a) {
   using T = typename Real<V>::T;
@@ -398,7 +404,7 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
     }
   }
   __syncthreads();
-  const V* res = fft_lines<V, +1>(b0, b1, s, ls, nl, tw);
+  const V* res = fft_lines<V, +1, MR>(b0, b1, s, ls, nl, tw);
   const bool want_wsum = a.red_wsum && b.st && b.st[slot].gauge;
   double dot = 0.0, wsum = 0.0;
   for (LineIter it(g.nx); it.l < nl; it.next()) {
@@ -450,14 +456,34 @@ static void set_smem(K kernel, size_t bytes) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Whether the schedule takes the radix-16 build of a kernel (FP64 only).
+template <typename V>
+static bool radix16(const FftSched& s) {
+  if constexpr (!std::is_same<V, double2>::value) {
+    return false;
+  } else {
+    for (int k = 0; k < s.nst; ++k)
+      if (s.radix[k] == 16) return true;
+    return false;
+  }
+}
+
+template <typename V, int MR>
+static void x_fwd_mr(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b, const PipeArgs& a,
+                     int nslots, size_t sm, cudaStream_t st) {
+  set_smem(k_x_fwd<V, MR>, sm);
+  count_launch();
+  k_x_fwd<V, MR><<<dim3(x_pass_blocks(g), 1, nslots), kThreads, sm, st>>>(g, s, tw, b, a);
+}
+
 template <typename V>
 void launch_x_fwd(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
                   const PipeArgs& a, int nslots, cudaStream_t st) {
   if (launch_xr_pass<V>(false, s.L, g, tw, b, a, nslots, st)) return;
   const size_t sm = x_lines_smem_bytes(s.L, g.lines_x, sizeof(V));
-  set_smem(k_x_fwd<V>, sm);
-  count_launch();
-  k_x_fwd<V><<<dim3(x_pass_blocks(g), 1, nslots), kThreads, sm, st>>>(g, s, tw, b, a);
+  if constexpr (std::is_same<V, double2>::value)
+    if (radix16<V>(s)) return x_fwd_mr<V, 16>(g, s, tw, b, a, nslots, sm, st);
+  x_fwd_mr<V, 8>(g, s, tw, b, a, nslots, sm, st);
 }
 
 template <typename V>
@@ -467,12 +493,24 @@ void launch_y(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
   dim3 grid((g.Hx + g.tile_y - 1) / g.tile_y, g.nz, nslots);
   const size_t sm = x_lines_smem_bytes(s.L, g.tile_y, sizeof(V));
   count_launch();
+  if constexpr (std::is_same<V, double2>::value) {
+    if (radix16<V>(s)) {
+      if (inverse) {
+        set_smem(k_y<V, +1, 16>, sm);
+        k_y<V, +1, 16><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
+      } else {
+        set_smem(k_y<V, -1, 16>, sm);
+        k_y<V, -1, 16><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
+      }
+      return;
+    }
+  }
   if (inverse) {
-    set_smem(k_y<V, +1>, sm);
-    k_y<V, +1><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
+    set_smem(k_y<V, +1, 8>, sm);
+    k_y<V, +1, 8><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
   } else {
-    set_smem(k_y<V, -1>, sm);
-    k_y<V, -1><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
+    set_smem(k_y<V, -1, 8>, sm);
+    k_y<V, -1, 8><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
   }
 }
 
@@ -482,9 +520,16 @@ void launch_z(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
   if (launch_col_pass<V>(2, s.L, g, tw, b, a, nslots, st)) return;
   dim3 grid((g.Hx + g.tile_z - 1) / g.tile_z, g.Py, nslots);
   const size_t sm = x_lines_smem_bytes(s.L, g.tile_z, sizeof(V));
-  set_smem(k_z<V>, sm);
   count_launch();
-  k_z<V><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
+  if constexpr (std::is_same<V, double2>::value) {
+    if (radix16<V>(s)) {
+      set_smem(k_z<V, 16>, sm);
+      k_z<V, 16><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
+      return;
+    }
+  }
+  set_smem(k_z<V, 8>, sm);
+  k_z<V, 8><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
 }
 
 template <typename V>
@@ -492,9 +537,16 @@ void launch_x_inv(const PassGeom& g, const FftSched& s, const V* tw, const Batch
                   const PipeArgs& a, int nslots, cudaStream_t st) {
   if (launch_xr_pass<V>(true, s.L, g, tw, b, a, nslots, st)) return;
   const size_t sm = x_lines_smem_bytes(s.L, g.lines_x, sizeof(V));
-  set_smem(k_x_inv<V>, sm);
   count_launch();
-  k_x_inv<V><<<dim3(x_pass_blocks(g), 1, nslots), kThreads, sm, st>>>(g, s, tw, b, a);
+  if constexpr (std::is_same<V, double2>::value) {
+    if (radix16<V>(s)) {
+      set_smem(k_x_inv<V, 16>, sm);
+      k_x_inv<V, 16><<<dim3(x_pass_blocks(g), 1, nslots), kThreads, sm, st>>>(g, s, tw, b, a);
+      return;
+    }
+  }
+  set_smem(k_x_inv<V, 8>, sm);
+  k_x_inv<V, 8><<<dim3(x_pass_blocks(g), 1, nslots), kThreads, sm, st>>>(g, s, tw, b, a);
 }
 
 #define GPS_INSTANTIATE(V)                                                                       \

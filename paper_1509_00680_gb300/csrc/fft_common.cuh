@@ -62,6 +62,43 @@ template <typename V, int DIR> struct Dft<V, DIR, 8> {
   }
 };
 
+// 16 points as two 8-point transforms of the even and odd elements joined by
+// the twiddles e^{DIR 2 pi i k / 16}, k = 0..7.
+template <typename V, int DIR> struct Dft<V, DIR, 16> {
+  __device__ __forceinline__ static V rot(V a, typename Real<V>::T cr, typename Real<V>::T sr) {
+    // a (cr + i DIR sr)
+    using T = typename Real<V>::T;
+    const T si = DIR < 0 ? -sr : sr;
+    return mk<V>(a.x * cr - a.y * si, a.x * si + a.y * cr);
+  }
+  __device__ __forceinline__ static void run(V* x) {
+    using T = typename Real<V>::T;
+    const T c1 = (T)0.92387953251128675613;   // cos(pi/8)
+    const T s1 = (T)0.38268343236508977173;   // sin(pi/8)
+    const T c = (T)0.70710678118654752440;    // sqrt(1/2)
+    V e[8], o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      e[k] = x[2 * k];
+      o[k] = x[2 * k + 1];
+    }
+    Dft<V, DIR, 8>::run(e);
+    Dft<V, DIR, 8>::run(o);
+    o[1] = rot(o[1], c1, s1);
+    o[2] = rot(o[2], c, c);
+    o[3] = rot(o[3], s1, c1);
+    o[4] = DIR < 0 ? mk<V>(o[4].y, -o[4].x) : mk<V>(-o[4].y, o[4].x);
+    o[5] = rot(o[5], -s1, c1);
+    o[6] = rot(o[6], -c, c);
+    o[7] = rot(o[7], -c1, s1);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      x[k] = cadd(e[k], o[k]);
+      x[k + 8] = csub(e[k], o[k]);
+    }
+  }
+};
+
 template <typename V, int DIR> struct Dft<V, DIR, 3> {
   __device__ __forceinline__ static void run(V* x) {
     using T = typename Real<V>::T;

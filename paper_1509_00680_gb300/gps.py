@@ -89,6 +89,7 @@ _SIGS = {
     "gps_ionic_charge": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P,
                                         ctypes.POINTER(gps_electrolyte), _P, _P]),
     "gps_vacuum_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(gps_grid), _P, _P, _P]),
+    "gps_set_radix_order": (ctypes.c_int, [ctypes.c_int]),
     "gps_sccs_eps": (ctypes.c_int, [_P, ctypes.c_size_t, _P, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, _P, _P, _P]),
     "gps_polarization_charge": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P, _P, _P]),
@@ -315,6 +316,11 @@ class Context:
                                                _dev(phi), ctypes.byref(a), ctypes.byref(b),
                                                _stream(stream)), "gps_electrostatic_energy")
         return a.value, b.value
+
+
+def set_radix_order(order):
+    """-1: tune the FFT radix order (default); 0..3: use that order for new plans."""
+    _check(load().gps_set_radix_order(int(order)), "gps_set_radix_order")
 
 
 def make_request(grid, kind, rho, eps, phi, electrolyte=None, opts=None):

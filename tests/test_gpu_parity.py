@@ -117,6 +117,51 @@ def test_precondition_fp32_spectrum(gps, ctx, bc, n, h):
     assert relmax(N(v, g.shape), f.precondition(r)) < 2e-5
 
 
+# Grids whose padded lengths are multiples of 16 on most axes, so that the
+# radix-16 order (FP64 only) applies: 16, 32, 48, 64, 2048.
+RADIX = [
+    (synth.BC_PERIODIC, (32, 48, 64), (0.3, 0.3, 0.3)),
+    (synth.BC_FREE, (16, 24, 32), (0.5, 0.45, 0.4)),
+    (synth.BC_SURFACE, (32, 16, 24), (0.4, 0.45, 0.5)),
+    (synth.BC_WIRE, (24, 16, 40), (0.4, 0.5, 0.35)),
+    (synth.BC_PERIODIC, (8, 8, 2048), (0.5, 0.5, 0.01)),
+]
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+def test_fft_radix_orders(gps, order):
+    """Every radix order of the shared-memory FFT passes (gps_set_radix_order):
+    FP64 vacuum solve and preconditioner against the oracle; order 3 takes the
+    radix-16 kernels wherever a length has a factor 16."""
+    gps.set_radix_order(order)
+    c = gps.Context(0)
+    try:
+        for bc, n, h in RADIX:
+            g = _grid(bc, n, h)
+            rng = np.random.default_rng(21)
+            sigma = rng.standard_normal(g.shape)
+            w = T(np.zeros(g.shape))
+            c.vacuum_solve(gps.grid_from(g), T(sigma), w)
+            assert relmax(N(w, g.shape), VacuumSolver(g).apply(sigma)) < 1e-12
+            eps = 1.0 + 30.0 * rng.random(g.shape)
+            r = rng.standard_normal(g.shape)
+            f = Fields(g, eps)
+            v = T(np.zeros(g.shape))
+            c.precondition(gps.grid_from(g), T(f.s), T(r), v)
+            assert relmax(N(v, g.shape), f.precondition(r)) < 1e-12
+        if order == 3:
+            p = synth.workload(2, n=64, count=8)
+            phi = T(np.zeros(p.grid.shape))
+            rep = c.gpe_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), phi,
+                              gps.default_opts(tol_abs=0.0, tol_rel=1e-13, max_iter=2000))
+            ref, info = oracle.solve_gpe(p.grid, p.rho, p.eps, tol_abs=0.0, tol_rel=1e-13, max_iter=2000)
+            assert abs(rep.iters - info["iters"]) <= 2
+            assert rel2(N(phi, p.grid.shape), ref) <= 1e-10
+    finally:
+        c.close()
+        gps.set_radix_order(-1)
+
+
 # Grids whose padded x / y / z lengths are the powers of two 64 .. 1024 handled
 # by the register-resident kernels, with column tiles that end ragged
 # (Hx not a multiple of the columns per CTA); free-BC boxes are cubic in
