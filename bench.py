@@ -514,6 +514,55 @@ def run_dft(gps, device, flush):
     return res
 
 
+def run_experiments(args):
+    """The paper's GPe experiment (Sec. "Numerical results", Fig. NormrAcc) at
+    its own size: box 10, 300^3, phi a normalized Gaussian (sigma 0.5), eps the
+    erf cavity (d0 1.7, Delta 0.3, eps0 78.36), free, surface and periodic BC.
+    Accuracy (max |phi - phi_exact|, for periodic BC in the solver's gauge)
+    after k iterations of Algorithm 2 (PCG) and of Algorithm 1 (SC, eta =
+    0.6), FP64; one JSON line."""
+    import torch
+    from paper_1509_00680_gb300 import build
+    import synth
+    build.build()
+    from paper_1509_00680_gb300 import gps
+    dev = torch.device("cuda", 0)
+    ctx = gps.Context(0)
+    stream = torch.cuda.current_stream()
+    out = {"experiment": "E1 (Fig. NormrAcc)", "n": args.exp_n, "box": 10.0, "bcs": {}}
+    pcg_ks, sc_ks = (1, 2, 3, 4, 5, 6, 8, 10, 12, 15, 20), (5, 10, 20, 40, 80)
+    for bc in (synth.BC_FREE, synth.BC_SURFACE, synth.BC_PERIODIC):
+        p = synth.manufactured(n=args.exp_n, bc=bc)
+        g = gps.grid_from(p.grid)
+        rho = torch.from_numpy(p.rho.ravel()).to(dev)
+        eps = torch.from_numpy(p.eps.ravel()).to(dev)
+        ex = torch.from_numpy(p.phi_exact.ravel()).to(dev)
+        periodic = bc == synth.BC_PERIODIC
+        sq = torch.sqrt(eps)
+        ex_g = ex - (sq * ex).sum() / sq.sum() if periodic else ex     # the solver's gauge
+        row = {}
+        for name, ks, kw in (("pcg", pcg_ks, {}), ("sc", sc_ks, dict(method=gps.GPS_SC, eta=0.6))):
+            pts = []
+            for k in ks:
+                phi = torch.zeros_like(rho)
+                o = gps.default_opts(tol_abs=0.0, max_iter=k, **kw)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rep = ctx.gpe_solve(g, rho, eps, phi, o, allow=(gps.GPS_OK, gps.GPS_ERR_NOT_CONVERGED))
+                e1.record(stream)
+                e1.synchronize()
+                ref = ex_g if not (periodic and name == "sc") else ex - ex.mean()
+                got = phi if not (periodic and name == "sc") else phi - phi.mean()
+                pts.append({"iters": rep.iters, "res": rep.res, "accuracy": (got - ref).abs().max().item(),
+                            "ms": e0.elapsed_time(e1)})
+            row[name] = pts
+        out["bcs"][synth.BC_NAMES[bc]] = row
+        del rho, eps, ex, ex_g, sq
+        torch.cuda.empty_cache()
+    ctx.close()
+    print(json.dumps(out))
+
+
 def run_serving(gps, device, args, count=None):
     """Bounded sample of the serving workload: requests drawn like the
     512-request stream (edges {48,64,96,128,192}, BC and problem mixed,
@@ -795,9 +844,15 @@ def main():
     ap.add_argument("--passes", default=None, choices=sorted(PASS_CASES),
                     help="per-pass times of one preconditioner application instead of the bench")
     ap.add_argument("--precisions", default="fp64,df64,fp32")
+    ap.add_argument("--experiments", action="store_true",
+                    help="the paper's GPe convergence experiment (accuracy vs iterations) instead of the bench")
+    ap.add_argument("--exp-n", type=int, default=300, help="grid points per side of --experiments")
     args = ap.parse_args()
     if args.passes:
         run_passes(args)
+        return
+    if args.experiments:
+        run_experiments(args)
         return
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -295,6 +295,30 @@ def free_union(n=256, h=0.3, count=200, margin=10.0, kind="nlpb", conc=0.5, seed
                    charges=charges, spheres=spheres, tol_abs=1e-10)
 
 
+def manufactured(n=300, L=10.0, bc=BC_FREE, sigma=0.5, d0=1.7, delta=0.3, eps0=EPS_WATER):
+    """The paper's GPe test (Sec. "Numerical results"): a cubic box of edge L
+    with n points per side, phi a normalized Gaussian of width sigma at the
+    centre, eps = 1 + (eps0 - 1) h(d0, delta; r), and rho = -(1/4 pi) div eps
+    grad phi in closed form (radial functions).  The Gaussian is negligible
+    at the faces (exp(-L^2 / 8 sigma^2)), so the same fields serve every BC.
+    Returns the Problem with the exact potential in `phi_exact`."""
+    from scipy.special import erf
+    h = L / n
+    grid = Grid(n, n, n, h, h, h, bc)
+    c = n // 2 * h
+    x = h * np.arange(n)
+    r = np.sqrt((x[:, None, None] - c) ** 2 + (x[None, :, None] - c) ** 2 + (x[None, None, :] - c) ** 2)
+    phi = np.exp(-r * r / (2 * sigma * sigma)) / (2 * np.pi * sigma * sigma) ** 1.5
+    lap = (r * r / sigma ** 4 - 3.0 / sigma ** 2) * phi
+    dphi = -(r / sigma ** 2) * phi
+    eps = 1.0 + (eps0 - 1.0) * 0.5 * (1.0 + erf((r - d0) / delta))
+    deps = (eps0 - 1.0) / (delta * np.sqrt(np.pi)) * np.exp(-((r - d0) / delta) ** 2)
+    rho = -(eps * lap + deps * dphi) / (4.0 * np.pi)
+    prob = Problem("manufactured_%s_%d" % (BC_NAMES[bc], n), grid, rho, eps, eps0=eps0, tol_abs=1e-10)
+    prob.phi_exact = phi
+    return prob
+
+
 def wire_chain(n=32, nz=48, h=0.35, count=3, radius=2.4, conc=0.3, kind="lpb"):
     """Wire BC (periodic z, free x and y): `count` cavities of radius `radius`
     (Delta = 0.5) evenly spaced along z on the box axis, each holding a pair
