@@ -254,6 +254,22 @@ def test_wire_nlpb(gps, ctx):
     assert rel2(N(phi, p.grid.shape), ref) <= 1e-9
 
 
+def test_lpb_manufactured_solution(gps, ctx):
+    """The paper's linear-PB test on the GPU (free BC, the library's own
+    lambda from the electrolyte): the analytic potential to the
+    discretization accuracy the oracle reaches (6e-6 of the peak at 96^3)."""
+    import math
+    p = synth.manufactured(n=96, L=16.0, sigma=1.0, d0=2.5, delta=0.5)
+    e = synth.Electrolyte((1, -1), (0.5, 0.5), 300.0)
+    lam = oracle.pb.linear_lambda(oracle.pb.exclusion_from_eps(p.eps, p.eps0), e)
+    rho = p.rho + lam * p.phi_exact / (4 * math.pi)
+    el = gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.pb_solve(gps.grid_from(p.grid), T(rho), T(p.eps), el, "lpb", phi, gps.default_opts(tol_abs=1e-11))
+    assert rep.status == 0 and rep.iters <= 25
+    assert np.abs(N(phi, p.grid.shape) - p.phi_exact).max() < 2e-5 * p.phi_exact.max()
+
+
 def test_gpe_free_single_cavity(gps, ctx):
     p = synth.workload(1)          # 64^3, h = 0.3, the free-BC workload itself
     got, ref, rep, info = _solve_pair(gps, ctx, p)

@@ -293,6 +293,25 @@ def test_paper_manufactured_solution_free():
     assert np.abs(phi - phi_ex).max() < 5e-5 * phi_ex.max()
 
 
+def test_lpb_manufactured_solution_free():
+    """The paper's linear-PB test (Sec. "Numerical performances" of the PB
+    section): phi a normalized Gaussian, eps the erf cavity, rho = -(1/4pi)
+    (div eps grad phi - lambda phi) in closed form, free BC.  The Gaussian
+    (sigma 1, cavity d0 = 2.5, box 16, 0.5 M) reaches into the solvent, so the
+    ionic term matters: with lambda dropped or of the wrong sign the error is
+    ~200x larger than the discretization error (6e-6) of the right one."""
+    p = synth.manufactured(n=96, L=16.0, sigma=1.0, d0=2.5, delta=0.5)
+    el = synth.Electrolyte((1, -1), (0.5, 0.5), 300.0)
+    lam = pb.linear_lambda(pb.exclusion_from_eps(p.eps, p.eps0), el)
+    rho = p.rho + lam * p.phi_exact / (4 * math.pi)
+    top = p.phi_exact.max()
+    phi, info = oracle.solve_lpb(p.grid, rho, p.eps, lam, tol_abs=1e-11, max_iter=400)
+    assert info["iters"] <= 25                  # the paper: ~1e-10 in about ten iterations
+    assert np.abs(phi - p.phi_exact).max() < 2e-5 * top
+    wrong, _ = oracle.solve_lpb(p.grid, rho, p.eps, -lam, tol_abs=1e-11, max_iter=400)
+    assert np.abs(wrong - p.phi_exact).max() > 1e-3 * top
+
+
 def test_lpb_periodic_fourier_series():
     n, h = 32, 0.4
     g = synth.Grid(n, n, n, h, h, h, synth.BC_PERIODIC)
