@@ -270,6 +270,22 @@ def test_lpb_manufactured_solution(gps, ctx):
     assert np.abs(N(phi, p.grid.shape) - p.phi_exact).max() < 2e-5 * p.phi_exact.max()
 
 
+def test_mpb_manufactured_solution(gps, ctx):
+    """The paper's modified-PB test on the GPU (p = 0.74, R = 3 angstrom,
+    100 mol/m^3, free BC, FP64 Newton outer loop): the analytic potential to
+    the discretization accuracy of 96^3 in a few outer steps."""
+    p = synth.manufactured(n=96, L=16.0, sigma=1.0, d0=2.5, delta=0.5)
+    e = synth.Electrolyte((1, -1), (0.1, 0.1), 300.0, radius_angstrom=(3.0, 3.0), packing=0.74)
+    rho = p.rho - oracle.pb.ionic_charge(p.phi_exact, oracle.pb.exclusion_from_eps(p.eps, p.eps0), e)
+    el = gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0, radius_angstrom=e.radius_angstrom,
+                              packing=e.packing)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.pb_solve(gps.grid_from(p.grid), T(rho), T(p.eps), el, "mpb", phi,
+                       gps.default_opts(tol_outer=1e-10, max_iter=500))
+    assert rep.status == 0 and rep.outer_iters <= 8
+    assert np.abs(N(phi, p.grid.shape) - p.phi_exact).max() < 2e-5 * p.phi_exact.max()
+
+
 def test_gpe_free_single_cavity(gps, ctx):
     p = synth.workload(1)          # 64^3, h = 0.3, the free-BC workload itself
     got, ref, rep, info = _solve_pair(gps, ctx, p)
