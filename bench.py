@@ -114,7 +114,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel on this workload, from the ncu capture summarized in
 # profiles/k_z_gpe_periodic_128.md (to be retaken whenever the kernel changes).
-NCU_TRAFFIC = {"z": 19354112}
+NCU_TRAFFIC = {"z": 19335936}
 
 
 def pass_geometry(grid):
