@@ -120,6 +120,12 @@ typedef struct {
    * other problems. */
   double radius_angstrom[GPS_MAX_SPECIES];
   double packing;
+  /* Ion-exclusion function gamma(r) >= 0 of Eq. (rhoions), nx*ny*nz values, or
+   * NULL for the cavity function gamma = (eps - 1)/(eps0 - 1).  A device array
+   * for gps_pb_solve and gps_ionic_charge, a host array for gps_pb_solve_host;
+   * must be NULL in batched and served requests.  A solve with it takes no
+   * warm start. */
+  const double* exclusion;
 } gps_electrolyte;
 
 /* Solver options.  Convergence of Algorithm 2 is tested on the Euclidean norm

@@ -603,7 +603,7 @@ struct Pool {
   size_t n = 0, wn = 0;
   int pstride = 0;
   Fields f{};
-  double *own_rho = nullptr, *own_eps = nullptr, *own_phi = nullptr;
+  double *own_rho = nullptr, *own_eps = nullptr, *own_phi = nullptr, *own_gam = nullptr;
   double2* W64 = nullptr;
   float2* W32 = nullptr;
   double *partials = nullptr, *partials2 = nullptr, *partials3 = nullptr;
@@ -1230,6 +1230,7 @@ struct Engine {
       if (v == GPS_OK && (r->req.kind < GPS_GPE || r->req.kind > GPS_MPB)) v = GPS_ERR_INVALID;
       if (v == GPS_OK && r->req.kind == GPS_MPB) v = validate_steric(&r->req.el);
       if (v == GPS_OK && r->req.opts.method != GPS_PCG) v = GPS_ERR_INVALID;   // single solves only
+      if (v == GPS_OK && r->req.el.exclusion) v = GPS_ERR_INVALID;            // single solves only
       if (v == GPS_OK && (!r->req.rho_host || !r->req.eps_host || !r->req.phi_host)) v = GPS_ERR_INVALID;
       if (v != GPS_OK) {
         r->status = v;
@@ -1322,7 +1323,8 @@ int solve_direct(Pool& P, const double* rho, const double* eps, double* phi, int
   SlotState s = initial_state(kind, el, o);
   // warm start: same kind, same electrolyte (LPB) and eps equal value by
   // value to the previous warm-start solve's
-  const bool keep = o.warm_start && kind != GPS_NLPB && kind != GPS_MPB;
+  const bool keep = o.warm_start && kind != GPS_NLPB && kind != GPS_MPB && !(el && el->exclusion);
+  P.f.gam = (kind != GPS_GPE && el) ? el->exclusion : nullptr;
   P.f.wphi = nullptr;
   P.f.wd = nullptr;
   if (keep) {
@@ -1398,6 +1400,7 @@ int solve_direct(Pool& P, const double* rho, const double* eps, double* phi, int
   P.f.rho = P.own_rho;
   P.f.eps = P.own_eps;
   P.f.phi = P.own_phi;
+  P.f.gam = nullptr;
   fill_report(rep, P.st_host[0], t0);
   return P.st_host[0].status;
 }
@@ -1780,7 +1783,16 @@ int gps_pb_solve_host(gps_ctx* ctx, const gps_grid* grid, const double* rho_h, c
   const size_t b = P->n * sizeof(double);
   ck(cudaMemcpyAsync(P->own_rho, rho_h, b, cudaMemcpyHostToDevice, st));
   ck(cudaMemcpyAsync(P->own_eps, eps_h, b, cudaMemcpyHostToDevice, st));
-  int s = o.method == GPS_PCG ? solve_direct(*P, P->own_rho, P->own_eps, P->own_phi, kind, el, o, rep, st, t0)
+  gps_electrolyte eld{};
+  const gps_electrolyte* elp = el;
+  if (el && el->exclusion && kind != GPS_GPE) {   // host array: copied next to rho and eps
+    if (!P->own_gam) P->own_gam = P->mem.alloc<double>(P->n);
+    ck(cudaMemcpyAsync(P->own_gam, el->exclusion, b, cudaMemcpyHostToDevice, st));
+    eld = *el;
+    eld.exclusion = P->own_gam;
+    elp = &eld;
+  }
+  int s = o.method == GPS_PCG ? solve_direct(*P, P->own_rho, P->own_eps, P->own_phi, kind, elp, o, rep, st, t0)
                               : solve_comparison(*P, P->own_rho, P->own_eps, P->own_phi, o, rep, st, t0);
   ck(cudaMemcpyAsync(phi_h, P->own_phi, b, cudaMemcpyDeviceToHost, st));
   s = finish(s, st);
@@ -1887,7 +1899,7 @@ int gps_ionic_charge(gps_ctx* ctx, const gps_grid* grid, const double* phi, cons
   const size_t n = (size_t)grid->nx * grid->ny * grid->nz;
   const bool steric = el->packing > 0;
   if (steric && validate_steric(el) != GPS_OK) return GPS_ERR_INVALID;
-  launch_ionic_charge(phi, eps, out, n, ion_params(el, steric), st);
+  launch_ionic_charge(phi, eps, el->exclusion, out, n, ion_params(el, steric), st);
   return finish(GPS_OK, st);
   GPS_GUARD_END
 }

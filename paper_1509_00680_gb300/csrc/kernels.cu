@@ -146,6 +146,13 @@ __global__ void k_fd16_q(Batch b, Fields f, int nx, int ny, int nz, double ihx2,
   }
 }
 
+// Ion-exclusion function at element k of a slot: the caller's array when one
+// was given (single-slot pools only, so k is also its index), else the cavity
+// function (eps - 1)/(eps0 - 1).
+__device__ __forceinline__ double gamma_at(const double* gam, size_t k, double eps_k, const IonParams& ip) {
+  return gam ? gam[k] : (eps_k - 1.0) * ip.inv_eps0m1;
+}
+
 // Ionic charge gamma sum_i Z_i n_i[phi] and its derivative in phi (Eqs.
 // rhoions, ionsconcPB; with ip.steric the Bikerman denominator of Eq.
 // ionsconcMPB, 1 + sum_j a_j (e_j - 1), a_j = n_j^inf / n_j^max).  A
@@ -185,13 +192,13 @@ __global__ void k_setup_final(Batch b, Fields f, size_t n) {
   double lam_acc = 0.0, rho_acc = 0.0;
   GRID_STRIDE(i, n) {
     double lam = 0.0;
-    if (kind == GPS_LPB) lam = ip.lambda0 * (eps[i] - 1.0) * ip.inv_eps0m1;
+    if (kind == GPS_LPB) lam = ip.lambda0 * gamma_at(f.gam, off + i, eps[i], ip);
     qlam[i] = q[i] + lam;
     lam_acc += lam;
     rho_acc += rho[i];
     if (kind == GPS_NLPB) {
       double a, d;
-      ion_terms(0.0, (eps[i] - 1.0) * ip.inv_eps0m1, ip, &a, &d);
+      ion_terms(0.0, gamma_at(f.gam, off + i, eps[i], ip), ip, &a, &d);
       f.phi[off + i] = 0.0;
       f.rions[off + i] = a;
       f.rp[off + i] = rho[i];
@@ -421,7 +428,7 @@ __global__ void k_nl_eval(Batch b, Fields f, size_t n, double inv_p, int periodi
   GRID_STRIDE(i, n) {
     const size_t k = off + i;
     double a, d;
-    ion_terms(f.phi[k], (f.eps[k] - 1.0) * ip.inv_eps0m1, ip, &a, &d);
+    ion_terms(f.phi[k], gamma_at(f.gam, k, f.eps[k], ip), ip, &a, &d);
     const double lam = S.newton ? -kFourPi * d : 0.0;
     const double ri = f.rions[k], rp = f.rp[k];
     f.fresh[k] = a;
@@ -503,7 +510,7 @@ __global__ void k_nl_step(Batch b, Fields f, size_t n, int commit) {
       f.rp[k] = rpt;
     } else {
       double a, d;
-      ion_terms(ph, (f.eps[k] - 1.0) * ip.inv_eps0m1, ip, &a, &d);
+      ion_terms(ph, gamma_at(f.gam, k, f.eps[k], ip), ip, &a, &d);
       const double fr = a - rit + rpt;
       acc += fr * fr;
     }
@@ -521,10 +528,11 @@ __global__ void k_nl_step(Batch b, Fields f, size_t n, int commit) {
 }
 
 __global__ void k_ionic_charge(const double* __restrict__ phi, const double* __restrict__ eps,
-                               double* __restrict__ out, size_t n, IonParams ip) {
+                               const double* __restrict__ gam, double* __restrict__ out, size_t n,
+                               IonParams ip) {
   GRID_STRIDE(i, n) {
     double a, d;
-    ion_terms(phi[i], (eps[i] - 1.0) * ip.inv_eps0m1, ip, &a, &d);
+    ion_terms(phi[i], gamma_at(gam, i, eps[i], ip), ip, &a, &d);
     out[i] = a;
   }
 }
@@ -546,7 +554,7 @@ __global__ void k_fp_source(Batch b, Fields f, size_t n) {
     double src = f.rho[k] - bg - (nl ? f.q[k] : f.qlam[k]) * ph * inv4pi;
     if (nl) {
       double a, d;
-      ion_terms(ph, (f.eps[k] - 1.0) * ip.inv_eps0m1, ip, &a, &d);
+      ion_terms(ph, gamma_at(f.gam, k, f.eps[k], ip), ip, &a, &d);
       src += a;
     }
     f.tmp[k] = src;
@@ -792,10 +800,10 @@ void launch_table_split(const double* t, float* t32, float2* tdf, size_t n, cuda
   k_table_split<<<grid_blocks(n, kT), kT, 0, st>>>(t, t32, tdf, n);
 }
 
-void launch_ionic_charge(const double* phi, const double* eps, double* out, size_t n,
+void launch_ionic_charge(const double* phi, const double* eps, const double* gam, double* out, size_t n,
                          const IonParams& ip, cudaStream_t st) {
   count_launch();
-  k_ionic_charge<<<grid_blocks(n, kT), kT, 0, st>>>(phi, eps, out, n, ip);
+  k_ionic_charge<<<grid_blocks(n, kT), kT, 0, st>>>(phi, eps, gam, out, n, ip);
 }
 
 void launch_table_periodic(double* kern, double* lap, int Hx, int hy, int hz, double dkx, double dky,

@@ -24,6 +24,8 @@ struct Fields {
   double *tmp;                           // certificate source
   float *s32;                            // eps^-1/2 rounded to float (FP32 spectrum passes)
   const double *wphi, *wd;               // warm start: previous phi and b - r (slot 0 only)
+  const double* gam;                     // ion-exclusion function given by the caller (slot 0
+                                         // only); nullptr: the cavity function (eps-1)/(eps0-1)
 };
 
 int vec_blocks(size_t n, int nslots);
@@ -48,7 +50,7 @@ void launch_eps_differ(const double* a, const double* b, size_t n, int* flag, cu
 void launch_warm_store(const Batch& b, const Fields& f, double* weps, double* wphi, double* wd,
                        size_t n, cudaStream_t st);
 void launch_table_split(const double* t, float* t32, float2* tdf, size_t n, cudaStream_t st);
-void launch_ionic_charge(const double* phi, const double* eps, double* out, size_t n,
+void launch_ionic_charge(const double* phi, const double* eps, const double* gam, double* out, size_t n,
                          const IonParams& ip, cudaStream_t st);
 void launch_table_periodic(double* kern, double* lap, int Hx, int hy, int hz, double dkx, double dky,
                            double dkz, double inv_n, cudaStream_t st);

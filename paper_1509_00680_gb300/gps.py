@@ -36,7 +36,8 @@ class gps_electrolyte(ctypes.Structure):
     _fields_ = [("nspecies", ctypes.c_int), ("z", ctypes.c_int * GPS_MAX_SPECIES),
                 ("c_molar", ctypes.c_double * GPS_MAX_SPECIES),
                 ("temperature", ctypes.c_double), ("eps0", ctypes.c_double),
-                ("radius_angstrom", ctypes.c_double * GPS_MAX_SPECIES), ("packing", ctypes.c_double)]
+                ("radius_angstrom", ctypes.c_double * GPS_MAX_SPECIES), ("packing", ctypes.c_double),
+                ("exclusion", ctypes.c_void_p)]
 
 
 class gps_opts(ctypes.Structure):
@@ -154,9 +155,13 @@ def grid_from(g):
     return make_grid(g.nx, g.ny, g.nz, g.hx, g.hy, g.hz, g.bc)
 
 
-def make_electrolyte(z, c_molar, temperature=300.0, eps0=78.36, radius_angstrom=None, packing=0.0):
+def make_electrolyte(z, c_molar, temperature=300.0, eps0=78.36, radius_angstrom=None, packing=0.0,
+                     exclusion=None):
     """Electrolyte description; radius_angstrom (per species) and packing > 0
-    select the steric distribution of the modified PB problem ("mpb")."""
+    select the steric distribution of the modified PB problem ("mpb").
+    exclusion: the ion-exclusion function gamma on the grid, a float64 CUDA
+    tensor (device entry points) or a C-contiguous float64 numpy array
+    (host entry points); the caller keeps it alive while it is in use."""
     el = gps_electrolyte()
     el.nspecies = len(z)
     for i, (zi, ci) in enumerate(zip(z, c_molar)):
@@ -167,6 +172,8 @@ def make_electrolyte(z, c_molar, temperature=300.0, eps0=78.36, radius_angstrom=
     el.temperature = float(temperature)
     el.eps0 = float(eps0)
     el.packing = float(packing)
+    if exclusion is not None:
+        el.exclusion = _dev(exclusion) if hasattr(exclusion, "is_cuda") else _host(exclusion)
     return el
 
 

@@ -286,6 +286,58 @@ def test_mpb_manufactured_solution(gps, ctx):
     assert np.abs(N(phi, p.grid.shape) - p.phi_exact).max() < 2e-5 * p.phi_exact.max()
 
 
+def _custom_gamma(p):
+    """An ion-exclusion function other than the cavity function: its square
+    (ions kept further from the solute)."""
+    return oracle.pb.exclusion_from_eps(p.eps, p.eps0) ** 2
+
+
+def test_exclusion_function_lpb_and_host(gps, ctx):
+    p = synth.workload(3, nxy=32, nz=96, count=6, kind="lpb")
+    assert _has_solvent(p)
+    gam = np.ascontiguousarray(_custom_gamma(p))
+    e = p.electrolyte
+    gr = gps.grid_from(p.grid)
+    g_dev = T(gam)
+    el = gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0, exclusion=g_dev)
+    phi = T(np.zeros(p.grid.shape))
+    opts = gps.default_opts(tol_abs=0.0, tol_rel=1e-13, max_iter=2000, warm_start=1)
+    rep = ctx.pb_solve(gr, T(p.rho), T(p.eps), el, "lpb", phi, opts)
+    lam = oracle.pb.linear_lambda(gam, e)
+    ref, info = oracle.solve_lpb(p.grid, p.rho, p.eps, lam, tol_abs=0.0, tol_rel=1e-13, max_iter=2000)
+    got = N(phi, p.grid.shape)
+    assert rep.status == 0 and rep.warm == 0
+    assert rel2(got, ref) <= 1e-10
+    plain, _ = oracle.solve_lpb(p.grid, p.rho, p.eps, oracle.pb.linear_lambda(
+        oracle.pb.exclusion_from_eps(p.eps, p.eps0), e), tol_abs=0.0, tol_rel=1e-13, max_iter=2000)
+    assert rel2(got, plain) > 1e-6                 # the exclusion array was used
+    out = np.zeros(p.grid.npts)
+    el_h = gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0, exclusion=gam.ravel())
+    ctx.pb_solve_host(gr, np.ascontiguousarray(p.rho.ravel()), np.ascontiguousarray(p.eps.ravel()), el_h,
+                      "lpb", out, gps.default_opts(tol_abs=0.0, tol_rel=1e-13, max_iter=2000))
+    assert np.array_equal(out.reshape(p.grid.shape), got)
+    req = gps.make_request(gr, "lpb", np.ascontiguousarray(p.rho.ravel()), np.ascontiguousarray(p.eps.ravel()),
+                           np.zeros(p.grid.npts), el_h)
+    assert gps.batch_solve(ctx, [req], allow=(gps.GPS_OK, gps.GPS_ERR_INVALID))[0].status == gps.GPS_ERR_INVALID
+
+
+def test_exclusion_function_nlpb_and_ionic_charge(gps, ctx):
+    p = synth.workload(4, n=48, count=6, margin=5.0, kind="nlpb", conc=0.5)
+    gam = np.ascontiguousarray(_custom_gamma(p))
+    e = p.electrolyte
+    gr = gps.grid_from(p.grid)
+    g_dev = T(gam)                       # kept alive: the electrolyte holds its address only
+    el = gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0, exclusion=g_dev)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.pb_solve(gr, T(p.rho), T(p.eps), el, "nlpb", phi, gps.default_opts(tol_outer=1e-11, max_iter=3000))
+    ref, info = oracle.solve_nlpb(p.grid, p.rho, p.eps, e, p.eps0, tol=1e-11, max_iter=3000, gamma=gam)
+    assert info["converged"] and rep.status == 0
+    assert rel2(N(phi, p.grid.shape), ref) <= 1e-9
+    out = T(np.zeros(p.grid.shape))
+    ctx.ionic_charge(gr, T(ref), T(p.eps), el, out)
+    assert relmax(N(out, p.grid.shape), oracle.pb.ionic_charge(ref, gam, e)) < 1e-13
+
+
 def test_gpe_free_single_cavity(gps, ctx):
     p = synth.workload(1)          # 64^3, h = 0.3, the free-BC workload itself
     got, ref, rep, info = _solve_pair(gps, ctx, p)
