@@ -56,14 +56,17 @@ def test_struct_layout_matches_header(tmp_path):
                     'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gps_grid),'
                     ' sizeof(gps_electrolyte), sizeof(gps_opts), sizeof(gps_report),'
                     ' offsetof(gps_opts, precision), offsetof(gps_report, time_ms),'
-                    ' sizeof(gps_request), offsetof(gps_request, phi_host)); return 0;}\n')
+                    ' sizeof(gps_request), offsetof(gps_request, phi_host));'
+                    ' printf("%zu %zu %zu\\n", offsetof(gps_opts, diis), offsetof(gps_electrolyte, exclusion),'
+                    ' offsetof(gps_request, opts)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     want = [ctypes.sizeof(gps.gps_grid), ctypes.sizeof(gps.gps_electrolyte),
             ctypes.sizeof(gps.gps_opts), ctypes.sizeof(gps.gps_report),
             gps.gps_opts.precision.offset, gps.gps_report.time_ms.offset,
-            ctypes.sizeof(gps.gps_request), gps.gps_request.phi_host.offset]
+            ctypes.sizeof(gps.gps_request), gps.gps_request.phi_host.offset,
+            gps.gps_opts.diis.offset, gps.gps_electrolyte.exclusion.offset, gps.gps_request.opts.offset]
     assert [int(x) for x in out] == want
 
 
@@ -73,6 +76,29 @@ def test_default_opts_and_status_strings(lib):
     assert o.tol_abs == 1e-10 and o.max_iter == 500 and o.precision == gps.GPS_FP64
     assert gps.load().gps_status_string(gps.GPS_ERR_BREAKDOWN) == b"PCG breakdown"
     assert gps.load().gps_create(None, 0, 0) == gps.GPS_ERR_INVALID
+
+
+def test_new_defaults_and_host_side_argument_checks(lib):
+    """Defaults of the solver options and argument checks that return before
+    any CUDA call (NULL context or pointers, option ranges)."""
+    from paper_1509_00680_gb300 import gps
+    o = gps.default_opts()
+    assert o.forcing == 0.3 and o.eta == 0.6 and o.method == gps.GPS_PCG
+    assert o.alpha == 0.0 and o.diis == 0 and o.warm_start == 0 and o.mixed_switch == 1e-2
+    L = gps.load()
+    assert L.gps_set_radix_order(4) == gps.GPS_ERR_INVALID
+    assert L.gps_set_radix_order(-2) == gps.GPS_ERR_INVALID
+    assert L.gps_set_radix_order(-1) == gps.GPS_OK
+    g = gps.gps_grid()
+    rep = gps.gps_report()
+    assert L.gps_gpe_solve(None, ctypes.byref(g), None, None, None, ctypes.byref(o), ctypes.byref(rep),
+                           None) == gps.GPS_ERR_INVALID
+    assert L.gps_sccs_eps(None, 10, None, 5e-3, 1e-4, 78.36, None, None, None) == gps.GPS_ERR_INVALID
+    assert L.gps_polarization_charge(None, ctypes.byref(g), None, None, None, None, None) == gps.GPS_ERR_INVALID
+    assert L.gps_v_eps(None, ctypes.byref(g), None, None, None, None) == gps.GPS_ERR_INVALID
+    e1, e2 = ctypes.c_double(), ctypes.c_double()
+    assert L.gps_electrostatic_energy(None, ctypes.byref(g), None, None, None, ctypes.byref(e1), ctypes.byref(e2),
+                                      None) == gps.GPS_ERR_INVALID
 
 
 def test_product_path_has_no_oracle_dependency():
