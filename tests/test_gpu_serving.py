@@ -101,6 +101,40 @@ def test_batch_against_oracle(gps, ctx):
         assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
+def test_batch_with_wire_requests(gps, ctx):
+    """Wire-BC requests (three of one grid, so their pool holds several slots)
+    batched with a periodic and a free request: each potential bitwise equal
+    to its single solve; the wire GPe one also against the oracle."""
+    rng = np.random.default_rng(12)
+    reqs = []
+    for kind, mixed in (("gpe", False), ("lpb", True), ("nlpb", False)):
+        p = synth.wire_chain(n=24, nz=32, kind=kind)
+        opts = gps.default_opts(tol_abs=1e-10, max_iter=2000, tol_outer=1e-10,
+                                precision=gps.GPS_MIXED if mixed else gps.GPS_FP64)
+        el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+        reqs.append((p, kind, opts, el))
+    for bc, kind in ((synth.BC_PERIODIC, "gpe"), (synth.BC_FREE, "lpb")):
+        p = synth.serving_request(rng, 32, bc, kind, h=0.45)
+        el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+        reqs.append((p, kind, gps.default_opts(tol_abs=1e-10, max_iter=2000), el))
+    alone = _alone(gps, ctx, reqs)
+    keep, rs = [], []
+    for p, kind, opts, el in reqs:
+        rho = np.ascontiguousarray(p.rho.ravel())
+        eps = np.ascontiguousarray(p.eps.ravel())
+        phi = np.full(p.grid.npts, np.nan)
+        keep.append((rho, eps, phi))
+        rs.append(gps.make_request(gps.grid_from(p.grid), kind, rho, eps, phi, el, opts))
+    reps = gps.batch_solve(ctx, rs)
+    for (phi_a, rep_a), (_, _, phi_b), rep_b in zip(alone, keep, reps):
+        assert rep_b.status == 0 and rep_a.status == 0 and rep_a.iters == rep_b.iters
+        assert np.array_equal(phi_a, phi_b)
+    p = reqs[0][0]
+    ref, _ = oracle.solve_gpe(p.grid, p.rho, p.eps, tol_abs=1e-10, max_iter=2000)
+    got = keep[0][2].reshape(ref.shape)
+    assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
 def test_server_stream_identical_to_alone(gps, ctx):
     reqs = _requests(gps, count=12, seed=11)
     alone = _alone(gps, ctx, reqs)
