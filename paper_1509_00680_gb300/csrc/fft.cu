@@ -27,7 +27,10 @@ namespace gps {
 // leaves k unchanged), without a division per butterfly.  When L/R (FL) or
 // Ns (FS) is a multiple of the padding period, the padded index of element
 // r is the padded index of element 0 plus a constant times r.
-template <typename V, int DIR, int R, bool FL, bool FS>
+// HALF (first stage only, Ns = 1): elements L/2.. of every line are the zero
+// padding, i.e. x[R/2..R-1] of every butterfly; they are neither read nor
+// used (Dft::run_half).
+template <typename V, int DIR, int R, bool FL, bool FS, bool HALF = false>
 __device__ __forceinline__ void stage(const V* __restrict__ in, V* __restrict__ out, int L, int Ns,
                                       int ls, int nlines, const V* __restrict__ tw) {
   constexpr int P = 1 << PadShift<V>::v;
@@ -45,8 +48,8 @@ __device__ __forceinline__ void stage(const V* __restrict__ in, V* __restrict__ 
     V x[R];
     const int s0 = pidx<V>(j);
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = src[FL ? s0 + r * snb : pidx<V>(j + r * nb)];
-    if (k != 0) {
+    for (int r = 0; r < (HALF ? R / 2 : R); ++r) x[r] = src[FL ? s0 + r * snb : pidx<V>(j + r * nb)];
+    if (!HALF && k != 0) {
       const int step = tstep * k;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -54,7 +57,8 @@ __device__ __forceinline__ void stage(const V* __restrict__ in, V* __restrict__ 
         x[r] = DIR < 0 ? cmul(x[r], w) : cmulc(x[r], w);
       }
     }
-    Dft<V, DIR, R>::run(x);
+    if constexpr (HALF) Dft<V, DIR, R>::run_half(x);
+    else Dft<V, DIR, R>::run(x);
     const int base = (j - k) * R + k;
     const int d0 = pidx<V>(base);
 #pragma unroll
@@ -81,17 +85,44 @@ __device__ __forceinline__ void stage_any(const V* in, V* out, int L, int Ns, in
   else stage<V, DIR, R, false, false>(in, out, L, Ns, ls, nlines, tw);
 }
 
+// First stage (Ns = 1, so FS holds) of a line whose upper half is zero.
+template <typename V, int DIR, int R>
+__device__ __forceinline__ void stage_half(const V* in, V* out, int L, int ls, int nlines, const V* tw) {
+  constexpr int P = 1 << PadShift<V>::v;
+  if ((L / R) % P == 0) stage<V, DIR, R, true, false, true>(in, out, L, 1, ls, nlines, tw);
+  else stage<V, DIR, R, false, false, true>(in, out, L, 1, ls, nlines, tw);
+}
+
 // Full 1D transform of a batch of lines held in a; b is the ping-pong partner.
 // Returns the buffer holding the result.  Ends with a __syncthreads().
 // MR: the largest radix the kernel is built for (16 only in the FP64 kernels
 // launched for schedules that contain a radix-16 stage, so that the other
 // kernels keep their register budget).
-template <typename V, int DIR, int MR = 8>
-__device__ __forceinline__ V* fft_lines(V* a, V* b, const FftSched& s, int ls, int nlines, const V* tw) {
+// nin: elements of each line that may be nonzero (the rest is zero padding);
+// when it is exactly half the length the first stage is pruned (every padded
+// axis pads n to 2n, and the first radix of every schedule is even).
+template <typename V, int DIR, int MR = 8, bool PRUNE = true>
+__device__ __forceinline__ V* fft_lines(V* a, V* b, const FftSched& s, int ls, int nlines, const V* tw,
+                                        int nin) {
   V* in = a;
   V* out = b;
   for (int st = 0; st < s.nst; ++st) {
     const int R = s.radix[st], Ns = s.ns[st];
+    if (PRUNE && st == 0 && 2 * nin == s.L && R % 2 == 0) {
+      switch (R) {
+        case 2: stage_half<V, DIR, 2>(in, out, s.L, ls, nlines, tw); break;
+        case 4: stage_half<V, DIR, 4>(in, out, s.L, ls, nlines, tw); break;
+        case 16:
+          if constexpr (MR == 16) stage_half<V, DIR, 16>(in, out, s.L, ls, nlines, tw);
+          break;
+        default: stage_half<V, DIR, 8>(in, out, s.L, ls, nlines, tw); break;
+      }
+      __syncthreads();
+      V* t = in;
+      in = out;
+      out = t;
+      continue;
+    }
     switch (R) {
       case 2: stage_any<V, DIR, 2>(in, out, s.L, Ns, ls, nlines, tw); break;
       case 3: stage_any<V, DIR, 3>(in, out, s.L, Ns, ls, nlines, tw); break;
@@ -168,7 +199,9 @@ __device__ __forceinline__ void pair_offsets(const PassGeom& g, int p0, int nl, 
   }
 }
 
-template <typename V, int MR>
+// XH: the rows are zero-padded to twice their length (free and wire BC); a
+// separate build so that the unpadded one keeps its register budget.
+template <typename V, int MR, bool XH>
 __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, const V* __restrict__ twg,
                                                    Batch b, PipeArgs a) {
   using T = typename Real<V>::T;
@@ -220,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, cons
     }
   }
   __syncthreads();
-  const V* res = fft_lines<V, -1, MR>(b0, b1, s, ls, nl, tw);
+  const V* res = fft_lines<V, -1, MR, XH>(b0, b1, s, ls, nl, tw, g.nx);
   const T half = T(0.5);
   for (LineIter it(g.Hx); it.l < nl; it.next()) {
     const int l = it.l, k = it.j;
@@ -258,7 +291,7 @@ __global__ void __launch_bounds__(kThreads) k_y(PassGeom g, FftSched s, const V*
   V* col = W + plane + kx0 + c;
   if (act) load_column<V>(b0 + c * ls, col, g.Hx, y0, ystep, L, nload);
   __syncthreads();
-  const V* res = fft_lines<V, DIR, MR>(b0, b1, s, ls, nl, tw);
+  const V* res = fft_lines<V, DIR, MR>(b0, b1, s, ls, nl, tw, nload);
   const int nstore = DIR < 0 ? L : g.ny;  // inverse: crop to y < ny
   if (act) {
     const V* line = res + c * ls;
@@ -266,7 +299,9 @@ __global__ void __launch_bounds__(kThreads) k_y(PassGeom g, FftSched s, const V*
   }
 }
 
-template <typename V, int MR>
+// ZH: the columns are zero-padded to twice their length (free and surface BC);
+// a separate build, as for the x pass.
+template <typename V, int MR, bool ZH>
 __global__ void __launch_bounds__(kThreads) k_z(PassGeom g, FftSched s, const V* __restrict__ twg,
                                                Batch b, PipeArgs a) {
   using T = typename Real<V>::T;
@@ -292,7 +327,7 @@ __global__ void __launch_bounds__(kThreads) k_z(PassGeom g, FftSched s, const V*
   V* col = W + colbase + c;
   if (act) load_column<V>(b0 + c * ls, col, zstride, z0, zstep, L, g.nz);
   __syncthreads();
-  V* res = fft_lines<V, -1, MR>(b0, b1, s, ls, nl, tw);
+  V* res = fft_lines<V, -1, MR, ZH>(b0, b1, s, ls, nl, tw, g.nz);
   V* other = (res == b0) ? b1 : b0;
   const int kyp = min(ky, g.Py - ky);
   const int hy = g.Py / 2 + 1;
@@ -339,7 +374,7 @@ __global__ void __launch_bounds__(kThreads) k_z(PassGeom g, FftSched s, const V*
     }
   }
   __syncthreads();
-  const V* fin = fft_lines<V, +1, MR>(res, other, s, ls, nl, tw);
+  const V* fin = fft_lines<V, +1, MR, false>(res, other, s, ls, nl, tw, L);
   if (act) {
     const V* line = fin + c * ls;
     for (int z = z0; z < g.nz; z += zstep) col[(size_t)z * zstride] = line[pidx<V>(z)];
@@ -404,7 +439,7 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
     }
   }
   __syncthreads();
-  const V* res = fft_lines<V, +1, MR>(b0, b1, s, ls, nl, tw);
+  const V* res = fft_lines<V, +1, MR, false>(b0, b1, s, ls, nl, tw, L);
   const bool want_wsum = a.red_wsum && b.st && b.st[slot].gauge;
   double dot = 0.0, wsum = 0.0;
   for (LineIter it(g.nx); it.l < nl; it.next()) {
@@ -471,9 +506,14 @@ static bool radix16(const FftSched& s) {
 template <typename V, int MR>
 static void x_fwd_mr(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b, const PipeArgs& a,
                      int nslots, size_t sm, cudaStream_t st) {
-  set_smem(k_x_fwd<V, MR>, sm);
   count_launch();
-  k_x_fwd<V, MR><<<dim3(x_pass_blocks(g), 1, nslots), kThreads, sm, st>>>(g, s, tw, b, a);
+  if (2 * g.nx == s.L) {
+    set_smem(k_x_fwd<V, MR, true>, sm);
+    k_x_fwd<V, MR, true><<<dim3(x_pass_blocks(g), 1, nslots), kThreads, sm, st>>>(g, s, tw, b, a);
+  } else {
+    set_smem(k_x_fwd<V, MR, false>, sm);
+    k_x_fwd<V, MR, false><<<dim3(x_pass_blocks(g), 1, nslots), kThreads, sm, st>>>(g, s, tw, b, a);
+  }
 }
 
 template <typename V>
@@ -521,15 +561,26 @@ void launch_z(const PassGeom& g, const FftSched& s, const V* tw, const Batch& b,
   dim3 grid((g.Hx + g.tile_z - 1) / g.tile_z, g.Py, nslots);
   const size_t sm = x_lines_smem_bytes(s.L, g.tile_z, sizeof(V));
   count_launch();
+  const bool zh = 2 * g.nz == s.L;
   if constexpr (std::is_same<V, double2>::value) {
     if (radix16<V>(s)) {
-      set_smem(k_z<V, 16>, sm);
-      k_z<V, 16><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
+      if (zh) {
+        set_smem(k_z<V, 16, true>, sm);
+        k_z<V, 16, true><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
+      } else {
+        set_smem(k_z<V, 16, false>, sm);
+        k_z<V, 16, false><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
+      }
       return;
     }
   }
-  set_smem(k_z<V, 8>, sm);
-  k_z<V, 8><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
+  if (zh) {
+    set_smem(k_z<V, 8, true>, sm);
+    k_z<V, 8, true><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
+  } else {
+    set_smem(k_z<V, 8, false>, sm);
+    k_z<V, 8, false><<<grid, kThreads, sm, st>>>(g, s, tw, b, a);
+  }
 }
 
 template <typename V>

@@ -17,12 +17,16 @@ __device__ __forceinline__ V rot_i(V a) {  // a * (DIR * i)
 
 template <typename V, int DIR, int R> struct Dft;
 
+// run_half(x): the same transform when x[R/2..R-1] are zero (the zero-padded
+// half of a line in the first stage of a forward pass): X_(2m) is the R/2-point
+// transform of x[0..R/2-1], X_(2m+1) that of x_r w^r, w = e^{DIR 2 pi i / R}.
 template <typename V, int DIR> struct Dft<V, DIR, 2> {
   __device__ __forceinline__ static void run(V* x) {
     V a = x[0], b = x[1];
     x[0] = cadd(a, b);
     x[1] = csub(a, b);
   }
+  __device__ __forceinline__ static void run_half(V* x) { x[1] = x[0]; }
 };
 
 template <typename V, int DIR> struct Dft<V, DIR, 4> {
@@ -33,6 +37,14 @@ template <typename V, int DIR> struct Dft<V, DIR, 4> {
     x[2] = csub(a0, a2);
     x[1] = cadd(a1, a3);
     x[3] = csub(a1, a3);
+  }
+  __device__ __forceinline__ static void run_half(V* x) {
+    const V o = rot_i<V, DIR>(x[1]);
+    const V e0 = x[0], e1 = x[1];
+    x[0] = cadd(e0, e1);
+    x[2] = csub(e0, e1);
+    x[1] = cadd(e0, o);
+    x[3] = csub(e0, o);
   }
 };
 
@@ -58,6 +70,29 @@ template <typename V, int DIR> struct Dft<V, DIR, 8> {
     for (int k = 0; k < 4; ++k) {
       x[k] = cadd(e[k], o[k]);
       x[k + 4] = csub(e[k], o[k]);
+    }
+  }
+  __device__ __forceinline__ static void run_half(V* x) {
+    using T = typename Real<V>::T;
+    const T c = (T)0.70710678118654752440;  // sqrt(1/2)
+    V e[4] = {x[0], x[1], x[2], x[3]};
+    V o[4] = {x[0], x[1], x[2], x[3]};
+    // o_r *= e^{DIR 2 pi i r / 8}
+    if (DIR < 0) {
+      o[1] = mk<V>(c * (o[1].x + o[1].y), c * (o[1].y - o[1].x));
+      o[2] = mk<V>(o[2].y, -o[2].x);
+      o[3] = mk<V>(c * (o[3].y - o[3].x), -c * (o[3].x + o[3].y));
+    } else {
+      o[1] = mk<V>(c * (o[1].x - o[1].y), c * (o[1].x + o[1].y));
+      o[2] = mk<V>(-o[2].y, o[2].x);
+      o[3] = mk<V>(-c * (o[3].x + o[3].y), c * (o[3].x - o[3].y));
+    }
+    Dft<V, DIR, 4>::run(e);
+    Dft<V, DIR, 4>::run(o);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      x[2 * m] = e[m];
+      x[2 * m + 1] = o[m];
     }
   }
 };
@@ -95,6 +130,30 @@ template <typename V, int DIR> struct Dft<V, DIR, 16> {
     for (int k = 0; k < 8; ++k) {
       x[k] = cadd(e[k], o[k]);
       x[k + 8] = csub(e[k], o[k]);
+    }
+  }
+  __device__ __forceinline__ static void run_half(V* x) {
+    using T = typename Real<V>::T;
+    const T c1 = (T)0.92387953251128675613;   // cos(pi/8)
+    const T s1 = (T)0.38268343236508977173;   // sin(pi/8)
+    const T c = (T)0.70710678118654752440;    // sqrt(1/2)
+    V e[8], o[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) e[r] = x[r];
+    o[0] = x[0];
+    o[1] = rot(x[1], c1, s1);
+    o[2] = rot(x[2], c, c);
+    o[3] = rot(x[3], s1, c1);
+    o[4] = DIR < 0 ? mk<V>(x[4].y, -x[4].x) : mk<V>(-x[4].y, x[4].x);
+    o[5] = rot(x[5], -s1, c1);
+    o[6] = rot(x[6], -c, c);
+    o[7] = rot(x[7], -c1, s1);
+    Dft<V, DIR, 8>::run(e);
+    Dft<V, DIR, 8>::run(o);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      x[2 * m] = e[m];
+      x[2 * m + 1] = o[m];
     }
   }
 };
