@@ -357,15 +357,22 @@ void gps_server_destroy(gps_server* srv);
  * spectrum live in one file-scope device array of 8 MiB that every GPU
  * loading this library holds until the process exits.
  * Supported: GPS_BC_PERIODIC and GPS_BC_SURFACE grids whose padded FFT
- * lengths are even and factor into 2, 3 and 5, and whose spectrum
- * ((nx/2+1)*ny*nz complex doubles) plus twiddle and octant tables fit in the
- * 8 MiB array -- e.g. periodic grids up to 96^3.  Anything else returns
+ * lengths (nx, ny, and nz periodic or 2 nz surface) are even, at most 4096
+ * and factor into 2, 3 and 5, and for which
+ *     16 (nx + ny + Pz) + 8 (nx/2+1)(ny/2+1)(Pz/2+1) + 16 (nx/2+1) ny nz
+ * bytes (twiddles, Green's-function octant table, spectrum; each of the
+ * first four parts rounded up to 256 bytes) fit in the 8 MiB (8,388,608
+ * byte) array.  The largest cubic periodic grid is 96^3 (8,171,264 bytes);
+ * 96 x 96 x 100 and 100^3 are over the limit.  Anything else returns
  * GPS_ERR_INVALID.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call uses the same array and keeps the previous call's
- * contents: calls that overlap on the GPU (other streams, other host
- * threads) race with each other and must be serialized by the caller.
+ * device, with that device current) and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not use
+ * this entry point after cudaDeviceReset.  Every call uses the same array
+ * and keeps the previous call's contents (each call rebuilds its tables, and
+ * every spectrum value it reads it has written): calls that overlap on the
+ * GPU (other streams, other host threads) race with each other and must be
+ * serialized by the caller.
  * sigma_dev, w_dev: nx*ny*nz doubles on the current device.  The call
  * returns after synchronizing the stream. */
 int gps_vacuum_solve_noalloc(const gps_grid* grid, const double* sigma_dev, double* w_dev,

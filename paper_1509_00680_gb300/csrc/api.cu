@@ -387,13 +387,7 @@ struct Shape {
   DevMem mem;
 };
 
-int batch_lines(int L, int units) {
-  int b = 2048 / L;
-  if (b < 1) b = 1;
-  const int want = units / 304;   // keep >= ~2 CTAs per SM
-  if (want < b) b = want < 1 ? 1 : want;
-  return b;
-}
+int batch_lines(int L, int units) { return default_lines(L, units, sizeof(double2)); }
 
 void upload_twiddles(Shape* S, int L, double2** t64, float2** t32, dfc** tdf) {
   std::vector<double2> h64(L);
@@ -813,8 +807,8 @@ std::vector<int> batch_candidates(int b0, int L, size_t vbytes, bool fixed) {
     c.push_back(b0 < 1 ? 1 : b0);
     return c;
   }
-  for (int b = 1; b <= 16; ++b)
-    if (x_lines_smem_bytes(L, b, vbytes) <= 220 * 1024) c.push_back(b);
+  for (int b = 1; b <= kMaxLinesPerCta; ++b)
+    if (x_lines_smem_bytes(L, b, vbytes) <= kMaxLinesSmem) c.push_back(b);
   if (c.empty()) c.push_back(1);
   return c;
 }

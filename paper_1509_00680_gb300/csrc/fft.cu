@@ -162,6 +162,8 @@ struct LineIter {
 };
 
 constexpr int kMaxLinesX = 64;
+static_assert(kMaxLinesX >= kMaxLinesPerCta, "row-offset table of the x passes too small");
+static_assert(kThreads >= kMaxLinesPerCta, "the y and z passes need one thread per column");
 
 // Loads issued before their shared-memory stores, per thread and batch: the
 // stores go through generic pointers that the compiler must assume may alias
@@ -474,6 +476,16 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
 size_t x_lines_smem_bytes(int L, int lines, size_t vbytes) {
   const int ls = vbytes == sizeof(double2) ? line_stride<double2>(L) : line_stride<float2>(L);
   return (size_t)(L + 2 * lines * ls) * vbytes;
+}
+
+int default_lines(int L, int units, size_t vbytes) {
+  int b = 2048 / (L > 0 ? L : 1);
+  const int want = units / 304;   // keep >= ~2 CTAs per SM
+  if (want < b) b = want;
+  if (b > kMaxLinesPerCta) b = kMaxLinesPerCta;
+  if (b < 1) b = 1;
+  while (b > 1 && x_lines_smem_bytes(L, b, vbytes) > kMaxLinesSmem) --b;
+  return b;
 }
 
 int x_pass_blocks(const PassGeom& g) {

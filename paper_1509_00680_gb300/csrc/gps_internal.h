@@ -183,6 +183,15 @@ bool launch_col_pass(int mode, int L, const PassGeom& g, const V* tw, const Batc
                      const PipeArgs& a, int nslots, cudaStream_t st);
 size_t x_lines_smem_bytes(int L, int lines, size_t vbytes);
 int x_pass_blocks(const PassGeom& g);
+// Lines (x passes) or columns (y, z passes) per CTA that the shared-memory
+// kernels support: 1 .. kMaxLinesPerCta, with at most kMaxLinesSmem bytes of
+// shared memory (x_lines_smem_bytes).  The tuner tries every count in that
+// range; default_lines is the untuned choice for `units` lines of length L:
+// about 2048 elements per CTA while that leaves >= ~2 CTAs per SM, clamped to
+// the supported range.
+constexpr int kMaxLinesPerCta = 16;
+constexpr size_t kMaxLinesSmem = 220 * 1024;
+int default_lines(int L, int units, size_t vbytes);
 
 // ---- kernels.cu ------------------------------------------------------------
 int grid_blocks(size_t n, int threads);

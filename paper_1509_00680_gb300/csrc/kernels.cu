@@ -596,7 +596,7 @@ __global__ void k_table_periodic(double* __restrict__ kern, double* __restrict__
     const double kx = i * dkx, ky = j * dky, kz = k * dkz;
     const double k2 = kx * kx + ky * ky + kz * kz;
     kern[idx] = idx == 0 ? 0.0 : kFourPi / k2 * inv_n;
-    lap[idx] = -k2 * inv_n;
+    if (lap) lap[idx] = -k2 * inv_n;   // spectral Laplacian (periodic q); optional
   }
 }
 

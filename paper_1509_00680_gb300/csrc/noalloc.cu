@@ -26,7 +26,9 @@ std::mutex g_setup_mutex;
 
 // Host-side address of the array on the current device, found once per
 // device with that device current.  The symbol itself is only a host-side
-// stand-in and must never be passed to a kernel.
+// stand-in and must never be passed to a kernel.  The cached address belongs
+// to the device's primary context: it must not be used after
+// cudaDeviceReset (which the caller of this library must not mix with it).
 int scratch_address(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) return GPS_ERR_INVALID;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
@@ -60,14 +62,6 @@ bool radix_schedule(int L, gps::FftSched* s) {
   return rem == 1;
 }
 
-int lines_per_block(int L, int units) {
-  int b = 2048 / L;
-  if (b < 1) b = 1;
-  const int want = units / 304;
-  if (want < b) b = want < 1 ? 1 : want;
-  return b;
-}
-
 // tw[m] = exp(-2 pi i m / L) in FP64.
 __global__ void k_noalloc_twiddles(double2* tw, int L) {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < L; m += gridDim.x * blockDim.x) {
@@ -96,13 +90,12 @@ extern "C" int gps_vacuum_solve_noalloc(const gps_grid* grid, const double* sigm
     return GPS_ERR_INVALID;
   const int Hx = Px / 2 + 1, hy = Py / 2 + 1, hz = Pz / 2 + 1;
   const size_t table_n = (size_t)Hx * hy * hz;
-  // scratch layout: twiddles x, y, z | table | Laplacian table | spectrum
+  // scratch layout: twiddles x, y, z | Green's-function table | spectrum
   const size_t off_twx = 0;
   const size_t off_twy = off_twx + align256((size_t)Px * sizeof(double2));
   const size_t off_twz = off_twy + align256((size_t)Py * sizeof(double2));
   const size_t off_tab = off_twz + align256((size_t)Pz * sizeof(double2));
-  const size_t off_lap = off_tab + align256(table_n * sizeof(double));
-  const size_t off_w = off_lap + align256(table_n * sizeof(double));
+  const size_t off_w = off_tab + align256(table_n * sizeof(double));
   const size_t need = off_w + (size_t)Hx * Py * grid->nz * sizeof(double2);
   if (need > kScratchBytes) return GPS_ERR_INVALID;   // beyond the fixed scratch size
 
@@ -116,12 +109,12 @@ extern "C" int gps_vacuum_solve_noalloc(const gps_grid* grid, const double* sigm
   double2* twy = reinterpret_cast<double2*>(base + off_twy);
   double2* twz = reinterpret_cast<double2*>(base + off_twz);
   double* table = reinterpret_cast<double*>(base + off_tab);
-  double* lap = reinterpret_cast<double*>(base + off_lap);
   double2* W = reinterpret_cast<double2*>(base + off_w);
 
   // Tables are rebuilt on every call: the array keeps whatever the previous
   // call (of any grid) left in it.  The spectrum needs no clearing: every
   // entry a pass reads was written by the pass before it.
+  (void)cudaGetLastError();   // an earlier failed launch is not this call's error
   count_launch();
   k_noalloc_twiddles<<<(Px + 255) / 256, 256, 0, st>>>(twx, Px);
   count_launch();
@@ -132,7 +125,7 @@ extern "C" int gps_vacuum_solve_noalloc(const gps_grid* grid, const double* sigm
   const double dkx = 2 * kPi / (Px * grid->hx), dky = 2 * kPi / (Py * grid->hy),
                dkz = 2 * kPi / (Pz * grid->hz);
   if (grid->bc == GPS_BC_PERIODIC)
-    launch_table_periodic(table, lap, Hx, hy, hz, dkx, dky, dkz, inv_n, st);
+    launch_table_periodic(table, nullptr, Hx, hy, hz, dkx, dky, dkz, inv_n, st);
   else
     launch_table_surface(table, Hx, hy, hz, dkx, dky, dkz, grid->nz * grid->hz, inv_n, st);
 
@@ -140,9 +133,9 @@ extern "C" int gps_vacuum_solve_noalloc(const gps_grid* grid, const double* sigm
   g.nx = grid->nx; g.ny = grid->ny; g.nz = grid->nz;
   g.Px = Px; g.Py = Py; g.Pz = Pz; g.Hx = Hx;
   g.nrows = grid->ny * grid->nz;
-  g.lines_x = lines_per_block(Px, (g.nrows + 1) / 2);
-  g.tile_y = lines_per_block(Py, Hx * grid->nz);
-  g.tile_z = lines_per_block(Pz, Hx * Py);
+  g.lines_x = default_lines(Px, (g.nrows + 1) / 2, sizeof(double2));
+  g.tile_y = default_lines(Py, Hx * grid->nz, sizeof(double2));
+  g.tile_z = default_lines(Pz, Hx * Py, sizeof(double2));
   Batch b{};                 // one slot, no phase machine
   PipeArgs a{};
   a.in = sigma_dev;
