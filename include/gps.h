@@ -56,6 +56,9 @@ typedef enum {
  * are FP64 in all modes.
  *   GPS_FP64        FP64 spectrum.
  *   GPS_MIXED       FP64 spectrum until ||r|| <= mixed_switch ||r_0||, then FP32.
+ *                   For nonlinear PB r_0 is the residual of the first outer
+ *                   step (4 pi F_0): an inner solve that starts below the
+ *                   switch runs in FP32 throughout.
  *   GPS_DF64        double-float spectrum: each value the unevaluated sum of
  *                   two floats (about 48 significant bits), computed on the
  *                   FP32 pipe, which on GB300 issues 64x the FP64 rate.
@@ -144,7 +147,8 @@ typedef struct {
   double forcing;        /* NLPB Newton: cap of the inner solve's relative tolerance, which is
                             min(forcing, F/F_0) (F the outer residual); in (0, 1) */
   int precision;         /* gps_precision */
-  double mixed_switch;   /* GPS_MIXED: FP64 preconditioner until ||r|| <= mixed_switch*||r_0|| */
+  double mixed_switch;   /* GPS_MIXED(_DF64): high-precision preconditioner until
+                            ||r|| <= mixed_switch*||r_0|| (nonlinear PB: r_0 of the first outer step) */
   int certify;           /* 1: compute rep->fixed_point_res (always done for GPS_MIXED) */
   int warm_start;        /* GPe / LPB through the single-solve entry points: 1 = when the
                             previous solve of the same kind on this context and grid had the
@@ -381,16 +385,18 @@ int gps_vacuum_solve_noalloc(const gps_grid* grid, const double* sigma_dev, doub
 /* Instrumentation.  gps_set_profiling(ctx, mask): every kernel of a kind
  * whose bit is set in `mask` that the solve entry points launch is
  * bracketed by CUDA events on the call's stream, and the elapsed times are
- * collected when the call returns (mask 0 turns profiling off, 0x3FF times
+ * collected when the call returns (mask 0 turns profiling off, 0xFFFFF times
  * every kind).  Kernel kinds: 0 x_fwd, 1 y_fwd, 2 z (forward, Green's
- * multiply, inverse), 3 y_inv, 4 x_inv, 5 update_p, 6 update_r, 7 setup,
- * 8 stencil (the order-16 passes of GPS_SC / GPS_PSD), 9 sc_vector (their
- * vector updates and DIIS).
+ * multiply, inverse), 3 y_inv, 4 x_inv -- the spectrum passes of the FP64
+ * spectrum; 10-14 the same passes of the double-float spectrum and 15-19 of
+ * the FP32 spectrum; 5 update_p, 6 update_r, 7 setup, 8 stencil (the
+ * order-16 passes of GPS_SC / GPS_PSD), 9 sc_vector (their vector updates
+ * and DIIS).
  * Launches that return at once because the PCG had already converged are
  * not counted.  gps_get_profile writes per kind the launch count and the
  * total milliseconds accumulated since the last reset (arrays of
  * GPS_PROFILE_KINDS entries). */
-#define GPS_PROFILE_KINDS 10
+#define GPS_PROFILE_KINDS 20
 int gps_set_profiling(gps_ctx* ctx, int mask);
 int gps_get_profile(gps_ctx* ctx, long long* launches, double* total_ms, int reset);
 
@@ -402,6 +408,14 @@ int gps_get_profile(gps_ctx* ctx, long long* launches, double* total_ms, int res
  * plans and for tests of each order.  Clears the process-wide tuning cache;
  * shapes already planned in a context keep their plans (use a new context). */
 int gps_set_radix_order(int order);
+
+/* Kernels of the x passes of the FP32 spectrum, for reproducible plans and
+ * for tests of both: -1 (the default) the tuner times the shared-memory
+ * Stockham kernels against the register-resident ones (padded lengths 64 ..
+ * 1024) and keeps the faster; 0 always the shared-memory kernels; 1 the
+ * register-resident ones where the length allows.  Clears the process-wide
+ * tuning cache like gps_set_radix_order. */
+int gps_set_x_kernel(int kind);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 unsigned long long gps_kernel_launches(void);

@@ -736,11 +736,13 @@ void pipeline(Pool& P, const Batch& b, PipeArgs a, cudaStream_t st) {
   a.wstride = P.wn;
   const int ns = P.cap;
   const Shape::Sched& sc = S.sp[spec_of<V>()];
-  timed(0, b, st, [&](const Batch& bb) { launch_x_fwd<V>(sc.g, sc.fx, twx, bb, a, ns, st); });
-  timed(1, b, st, [&](const Batch& bb) { launch_y<V>(sc.g, sc.fy, twy, bb, a, false, ns, st); });
-  timed(2, b, st, [&](const Batch& bb) { launch_z<V>(sc.g, sc.fz, twz, bb, a, ns, st); });
-  timed(3, b, st, [&](const Batch& bb) { launch_y<V>(sc.g, sc.fy, twy, bb, a, true, ns, st); });
-  timed(4, b, st, [&](const Batch& bb) { launch_x_inv<V>(sc.g, sc.fx, twx, bb, a, ns, st); });
+  // profile kinds of the passes: 0-4 FP64 spectrum, 10-14 df64, 15-19 FP32
+  constexpr int k0 = spec_of<V>() == SPEC_FP64 ? 0 : spec_of<V>() == SPEC_DF64 ? 10 : 15;
+  timed(k0 + 0, b, st, [&](const Batch& bb) { launch_x_fwd<V>(sc.g, sc.fx, twx, bb, a, ns, st); });
+  timed(k0 + 1, b, st, [&](const Batch& bb) { launch_y<V>(sc.g, sc.fy, twy, bb, a, false, ns, st); });
+  timed(k0 + 2, b, st, [&](const Batch& bb) { launch_z<V>(sc.g, sc.fz, twz, bb, a, ns, st); });
+  timed(k0 + 3, b, st, [&](const Batch& bb) { launch_y<V>(sc.g, sc.fy, twy, bb, a, true, ns, st); });
+  timed(k0 + 4, b, st, [&](const Batch& bb) { launch_x_inv<V>(sc.g, sc.fx, twx, bb, a, ns, st); });
 }
 
 // ------------------------------------------------------------- autotuner --
@@ -765,6 +767,7 @@ struct TuneVal {
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune;
 int g_radix_order = -1;   // gps_set_radix_order: -1 tunes the radix order, else this one
+int g_x_kernel = -1;      // gps_set_x_kernel: -1 tuned, 0 shared-memory, 1 register-resident (FP32)
 
 template <typename F>
 float time_launch(F&& launch, cudaStream_t st) {
@@ -875,6 +878,7 @@ void tune_spec(Shape& S, cudaStream_t st) {
     const int norders = f64 ? 4 : 3;
     // x passes: lines per CTA and radix order of Px
     float tbest = 1e30f;
+    best.g.x_reg = 0;
     for (int lines : batch_candidates(S.g.lines_x, S.Px, sizeof(V), fixx))
       for (int order = 0; order < (fixx ? 1 : norders); ++order) {
         if (!fixx && !order_allowed(S.Px, order, norders)) continue;
@@ -886,6 +890,15 @@ void tune_spec(Shape& S, cudaStream_t st) {
                         time_launch([&] { launch_x_inv<V>(g, fx, twx, b, a, 1, st); }, st);
         if (t < tbest) { tbest = t; best.g.lines_x = lines; best.fx = fx; }
       }
+    // FP32 spectrum: the register-resident x kernels (power-of-two Px) as
+    // one more candidate against the shared-memory ones
+    if (std::is_same<V, float2>::value && col_pass_supported(S.Px) && g_x_kernel != 0) {
+      PassGeom g = best.g;
+      g.x_reg = 1;
+      const float t = time_launch([&] { launch_x_fwd<V>(g, best.fx, twx, b, a, 1, st); }, st) +
+                      time_launch([&] { launch_x_inv<V>(g, best.fx, twx, b, a, 1, st); }, st);
+      if (t < tbest || g_x_kernel == 1) { tbest = t; best.g.x_reg = 1; }
+    }
     tbest = 1e30f;
     for (int tile : batch_candidates(S.g.tile_y, S.Py, sizeof(V), fixy))
       for (int order = 0; order < (fixy ? 1 : norders); ++order) {
@@ -1023,6 +1036,7 @@ SlotState initial_state(int kind, const gps_electrolyte* el, const gps_opts& o) 
   s.spec_hi = df ? SPEC_DF64 : SPEC_FP64;
   s.spec = s.spec_hi;
   s.mixed = (o.precision == GPS_MIXED || o.precision == GPS_MIXED_DF64) ? 1 : 0;
+  s.mixed_req = s.mixed;
   s.mixed_switch = o.mixed_switch;
   s.certify = (o.certify || s.mixed) ? 1 : 0;
   s.newton = o.outer_mode == GPS_OUTER_NEWTON ? 1 : 0;
@@ -1150,9 +1164,9 @@ struct Engine {
     ensure_tuned(*P.shape, P.has_mixed, P.has_df64, P.stream);
     put_active(P, P.stream);
     const int m = 4;
-    // Pipelines of this round: the FP32 one if a slot iterates in FP32, a
-    // high-precision one if a slot is in (or, for nonlinear PB, may return
-    // to) that precision.  A slot that switches in mid-round waits for the
+    // Pipelines of this round: the FP32 one if a slot iterates in (or, for
+    // mixed nonlinear PB, may enter) FP32, a high-precision one if a slot is
+    // in (or, for nonlinear PB, may return to) that precision.  A slot that switches in mid-round waits for the
     // next round (the update kernels act only after their pipeline ran).
     const bool acc_mixed = P.has_mixed, acc_fp64 = P.has_fp64, acc_df64 = P.has_df64;
     bool lo = false, h64 = false, hdf = false;
@@ -1161,7 +1175,8 @@ struct Engine {
       const SlotState& s = P.st_host[k];
       if (s.phase == PH_DONE || s.phase == PH_IDLE) continue;
       const bool in_lo = s.spec == SPEC_FP32;
-      lo |= in_lo;
+      // a mixed nonlinear-PB slot may enter FP32 at any inner solve
+      lo |= in_lo || (s.kind == GPS_NLPB && s.mixed_req);
       if (!in_lo || s.kind == GPS_NLPB) (s.spec_hi == SPEC_FP64 ? h64 : hdf) = true;
     }
     P.has_mixed = acc_mixed && lo;
@@ -1874,6 +1889,12 @@ int gps_precondition(gps_ctx* ctx, const gps_grid* grid, const double* s, const 
   a.table = P->shape->table;
   a.table32 = P->shape->table32;
   a.tabledf = P->shape->tabledf;
+  if (precision == GPS_MIXED) {
+    // the FP32 passes read s as float, as inside the PCG (a copy made at setup)
+    launch_to_float(s, P->f.s32, P->n, st);
+    a.in_scale32 = P->f.s32;
+    a.out_scale32 = P->f.s32;
+  }
   if (precision == GPS_MIXED) pipeline<float2>(*P, b, a, st);
   else if (precision == GPS_DF64) pipeline<dfc>(*P, b, a, st);
   else pipeline<double2>(*P, b, a, st);
@@ -2082,6 +2103,14 @@ int gps_set_radix_order(int order) {
   if (order < -1 || order > 3) return GPS_ERR_INVALID;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_radix_order = order;
+  g_tune.clear();
+  return GPS_OK;
+}
+
+int gps_set_x_kernel(int kind) {
+  if (kind < -1 || kind > 1) return GPS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_x_kernel = kind;
   g_tune.clear();
   return GPS_OK;
 }

@@ -57,10 +57,13 @@ __host__ __device__ constexpr int stage_tw_size() { return stage_tw_offset<L, RE
 
 // Butterflies of one stage (radix R, Ns = NS) on the thread's E elements:
 // butterfly q is b = t + q L/E with inputs x[q R + r] = in[b + r L/R].
-// tws: this stage's twiddles W[r - 1][k].
-template <typename V, int L, int E, int DIR, int R, int NS>
+// tws: this stage's twiddles W[r - 1][k].  HALF (first stage only): the
+// inputs r >= R/2 are the zero padding of the line (rows >= L/2), so each
+// butterfly runs as two R/2-point ones (Dft::run_half).
+template <typename V, int L, int E, int DIR, int R, int NS, bool HALF = false>
 __device__ __forceinline__ void col_butterflies(V (&x)[E], int t, const V* tws) {
   constexpr int TPC = L / E, Q = E / R;
+  static_assert(!HALF || NS == 1, "zero-half pruning applies to the first stage");
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     if constexpr (NS > 1) {
@@ -71,7 +74,8 @@ __device__ __forceinline__ void col_butterflies(V (&x)[E], int t, const V* tws) 
         x[q * R + r] = DIR < 0 ? cmul(x[q * R + r], w) : cmulc(x[q * R + r], w);
       }
     }
-    Dft<V, DIR, R>::run(x + q * R);
+    if constexpr (HALF) Dft<V, DIR, R>::run_half(x + q * R);
+    else Dft<V, DIR, R>::run(x + q * R);
   }
 }
 
@@ -99,11 +103,12 @@ __device__ __forceinline__ void col_exchange(V (&x)[E], int t, V* line) {
 }
 
 // Stages S .. nst-1 of one transform.  On return x[q RL + r] = out[b + r L/RL]
-// with RL the radix of the last stage.
-template <typename V, int L, int E, int DIR, bool REV, int S>
+// with RL the radix of the last stage.  HALF: the transform's input is zero
+// beyond L/2 (pruned first stage).
+template <typename V, int L, int E, int DIR, bool REV, int S, bool HALF = false>
 __device__ __forceinline__ void col_stages(V (&x)[E], int t, const V* tw, V* line) {
   constexpr int R = ColPlan<L>::radix(S, REV), NS = ColPlan<L>::ns(S, REV);
-  col_butterflies<V, L, E, DIR, R, NS>(x, t, tw + stage_tw_offset<L, REV>(S));
+  col_butterflies<V, L, E, DIR, R, NS, HALF && S == 0>(x, t, tw + stage_tw_offset<L, REV>(S));
   if constexpr (S + 1 < ColPlan<L>::nst) {
     col_exchange<V, L, E, R, NS, ColPlan<L>::radix(S + 1, REV)>(x, t, line);
     col_stages<V, L, E, DIR, REV, S + 1>(x, t, tw, line);
@@ -147,7 +152,9 @@ __device__ __forceinline__ typename Real<V>::T real_of(double v) {
 }
 
 
-template <typename V, int L, int MODE>
+// HALF (forward y and z passes of zero-padded axes): rows >= L/2 of every
+// column are the padding; they are neither read nor transformed.
+template <typename V, int L, int MODE, bool HALF>
 __global__ void __launch_bounds__(kThreads, (ColCfg<V, L, MODE>::B)) k_col(PassGeom g, const V* __restrict__ twg, Batch b,
                                                  PipeArgs a) {
   constexpr int E = ColCfg<V, L, MODE>::E;
@@ -183,9 +190,10 @@ __global__ void __launch_bounds__(kThreads, (ColCfg<V, L, MODE>::B)) k_col(PassG
 #pragma unroll
     for (int r = 0; r < R0; ++r) {
       const int row = t + q * TPC + r * (L / R0);
-      x[q * R0 + r] = (act && row < nload) ? col[(size_t)row * stride] : czero<V>();
+      if (HALF && r >= R0 / 2) x[q * R0 + r] = czero<V>();
+      else x[q * R0 + r] = (act && row < nload) ? col[(size_t)row * stride] : czero<V>();
     }
-  col_stages<V, L, E, MODE == COL_Y_INV ? +1 : -1, false, 0>(x, t, tw, line);
+  col_stages<V, L, E, MODE == COL_Y_INV ? +1 : -1, false, 0, HALF>(x, t, tw, line);
   constexpr int RL = ColPlan<L>::radix(ColPlan<L>::nst - 1, false);
   if constexpr (MODE == COL_Z) {
     const int ky = blockIdx.y;
@@ -225,16 +233,29 @@ __global__ void __launch_bounds__(kThreads, (ColCfg<V, L, MODE>::B)) k_col(PassG
   }
 }
 
-template <typename V, int L, int MODE>
-void launch_col_len(const PassGeom& g, const V* tw, const Batch& b, const PipeArgs& a, int nslots,
-                    cudaStream_t st) {
+template <typename V, int L, int MODE, bool HALF>
+void launch_col_build(const PassGeom& g, const V* tw, const Batch& b, const PipeArgs& a, int nslots,
+                      cudaStream_t st) {
   constexpr int TC = kThreads / (L / ColCfg<V, L, MODE>::E);
   const size_t sm = (size_t)(TC * line_stride<V>(L)) * sizeof(V);
   if (sm + kStaticSmemAllowance > 48 * 1024)
-    cudaFuncSetAttribute(k_col<V, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_col<V, L, MODE, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const dim3 grid((g.Hx + TC - 1) / TC, MODE == COL_Z ? g.Py : g.nz, nslots);
   count_launch();
-  k_col<V, L, MODE><<<grid, kThreads, sm, st>>>(g, tw, b, a);
+  k_col<V, L, MODE, HALF><<<grid, kThreads, sm, st>>>(g, tw, b, a);
+}
+
+template <typename V, int L, int MODE>
+void launch_col_len(const PassGeom& g, const V* tw, const Batch& b, const PipeArgs& a, int nslots,
+                    cudaStream_t st) {
+  // zero-padded forward transforms: y of free and wire grids, z of free and surface grids
+  const bool half = (MODE == COL_Y_FWD && 2 * g.ny == L) || (MODE == COL_Z && 2 * g.nz == L);
+  if constexpr (MODE == COL_Y_INV) {
+    launch_col_build<V, L, MODE, false>(g, tw, b, a, nslots, st);
+  } else {
+    if (half) launch_col_build<V, L, MODE, true>(g, tw, b, a, nslots, st);
+    else launch_col_build<V, L, MODE, false>(g, tw, b, a, nslots, st);
+  }
 }
 
 template <typename V, int MODE>
@@ -266,6 +287,7 @@ __global__ void __launch_bounds__(kThreads, (ColCfg<V, L, 3>::B)) k_xr_fwd(PassG
   if (slot < 0) return;
   const double* __restrict__ in = a.in + slot * b.vstride;
   const double* __restrict__ scale = a.in_scale ? a.in_scale + slot * b.vstride : nullptr;
+  const float* __restrict__ scale32 = a.in_scale32 ? a.in_scale32 + slot * b.vstride : nullptr;
   V* __restrict__ W = reinterpret_cast<V*>(a.W) + slot * a.wstride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int l = threadIdx.x / TPC, t = threadIdx.x % TPC;
@@ -287,8 +309,8 @@ __global__ void __launch_bounds__(kThreads, (ColCfg<V, L, 3>::B)) k_xr_fwd(PassG
       T va = T(0), vb = T(0);
       if (act && j < g.nx) {
         const size_t o = (size_t)ra * g.nx + j;
-        va = load_scaled<V>(in, scale, o, red, sum);
-        if (hasb) vb = load_scaled<V>(in, scale, o + g.nx, red, sum);
+        va = load_scaled<V>(in, scale, o, red, sum, scale32);
+        if (hasb) vb = load_scaled<V>(in, scale, o + g.nx, red, sum, scale32);
       }
       x[q * R0 + r] = mk<V>(va, vb);
     }
@@ -327,6 +349,7 @@ __global__ void __launch_bounds__(kThreads, (ColCfg<V, L, 3>::B)) k_xr_inv(PassG
   const V* __restrict__ W = reinterpret_cast<const V*>(a.W) + slot * a.wstride;
   double* __restrict__ out = a.out + slot * b.vstride;
   const double* __restrict__ out_scale = a.out_scale ? a.out_scale + slot * b.vstride : nullptr;
+  const float* __restrict__ out_scale32 = a.out_scale32 ? a.out_scale32 + slot * b.vstride : nullptr;
   const double* __restrict__ dot_with = a.dot_with ? a.dot_with + slot * b.vstride : nullptr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int l = threadIdx.x / TPC, t = threadIdx.x % TPC;
@@ -370,13 +393,13 @@ __global__ void __launch_bounds__(kThreads, (ColCfg<V, L, 3>::B)) k_xr_inv(PassG
       if (act && j < g.nx) {
         const V zz = x[q * RL + r];
         const size_t oa = (size_t)ra * g.nx + j;
-        const double va = out_value<V>(zz.x, out_scale, oa);
+        const double va = out_value<V>(zz.x, out_scale, oa, out_scale32);
         out[oa] = va;
         if (dot_with) dot += va * dot_with[oa];
         if (want_wsum) wsum += unscaled<V>(zz.x);
         if (hasb) {
           const size_t ob = oa + g.nx;
-          const double vb = out_value<V>(zz.y, out_scale, ob);
+          const double vb = out_value<V>(zz.y, out_scale, ob, out_scale32);
           out[ob] = vb;
           if (dot_with) dot += vb * dot_with[ob];
           if (want_wsum) wsum += unscaled<V>(zz.y);
@@ -414,10 +437,12 @@ void launch_xr_len(bool inverse, const PassGeom& g, const V* tw, const Batch& b,
 template <typename V>
 bool launch_xr_pass(bool inverse, int L, const PassGeom& g, const V* tw, const Batch& b,
                     const PipeArgs& a, int nslots, cudaStream_t st) {
-  // Measured: faster for the df64 spectrum only.  The FP64 x passes are
-  // bound by the FP64 pipe and the FP32 ones by their FP64 input / output
-  // handling; both keep the shared-memory kernels.
-  if (!std::is_same<V, dfc>::value) return false;
+  // The df64 spectrum always takes these kernels (measured faster); the FP32
+  // spectrum where the tuner found them faster than the shared-memory ones
+  // (g.x_reg); the FP64 x passes are bound by the FP64 pipe and keep the
+  // shared-memory kernels.
+  if (std::is_same<V, double2>::value) return false;
+  if (std::is_same<V, float2>::value && !g.x_reg) return false;
   switch (L) {
     case 64: launch_xr_len<V, 64>(inverse, g, tw, b, a, nslots, st); return true;
     case 128: launch_xr_len<V, 128>(inverse, g, tw, b, a, nslots, st); return true;

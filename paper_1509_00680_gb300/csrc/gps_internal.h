@@ -78,6 +78,7 @@ struct SlotState {
   double F, F0, t, tol_outer, eta, forcing, lam_sum, eps_sum;
   double cert;          // ||g|| / ||phi||, -1 if not computed
   double rr_min;        // smallest ||r||^2 seen in the FP32 phase
+  double rr_switch;     // ||r||^2 below which the FP32 spectrum takes over (mixed)
   double ap_mean;       // periodic GPe: grid mean of A p removed in the r update
   double ap_sum, p_sum;
   int stall;            // FP32 iterations since the last new minimum
@@ -85,6 +86,7 @@ struct SlotState {
   int iter, max_iter, iters_total, fp64_iters;
   int use_k0, neutralize, gauge;
   int mixed, spec, spec_hi, restart, certify;   // spec: spectrum precision in use
+  int mixed_req;        // the caller asked for a mixed precision (nonlinear PB: each inner solve)
   int newton, outer, max_outer, bad_eps;
   // Set by the x inverse pass once v and (v, r) of this iteration exist,
   // and by update_p once p, A p and alpha do; each update kernel acts only
@@ -103,6 +105,7 @@ struct PassGeom {
   int nrows;           // ny*nz (rows of the x passes)
   int lines_x;         // row pairs per CTA in the x passes
   int tile_y, tile_z;  // columns per CTA in the y / z passes
+  int x_reg;           // FP32 spectrum: 1 = x passes by the register-resident kernels
 };
 
 // Slot addressing of one launch.  active == nullptr: slot 0 only, no phase

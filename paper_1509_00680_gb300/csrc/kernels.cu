@@ -282,6 +282,24 @@ __global__ void k_init(Batch b, Fields f, size_t n) {
     S.vdone = 0;
     S.pdone = 0;
     S.spec = S.spec_hi;
+    // nonlinear PB: an FP32 stall or breakdown returns one inner solve to the
+    // high precision, not the later ones (each starts from its own residual)
+    if (nl) S.mixed = S.mixed_req;
+    if (S.mixed) {
+      // FP32 spectrum once ||r|| <= mixed_switch ||r_ref||.  r_ref is r_0 of a
+      // linear solve; for nonlinear PB it is the first outer step's residual
+      // (4 pi F_0 in the units of r), so the inner solves of later outer
+      // steps whose residual is already that small run in FP32 from the
+      // start: the drift they add is bounded by the same eps_32 mixed_switch
+      // ||r_ref|| per solve as for a linear solve.
+      const double ref = nl ? kFourPi * kFourPi * S.F0 * S.F0 : S.rr0;
+      S.rr_switch = S.mixed_switch * S.mixed_switch * ref;
+      if (nl && S.rr0 <= S.rr_switch) {
+        S.spec = SPEC_FP32;
+        S.rr_min = S.rr0;
+        S.stall = 0;
+      }
+    }
     if (S.rr0 <= S.tol2) after_pcg(S);
     else S.phase = PH_ITER;
   }
@@ -314,18 +332,43 @@ __global__ void k_update_p(Batch b, Fields f, size_t n, double inv_n, int period
   const double beta = (S.iter == 0 || S.restart) ? 0.0 : vr / S.vr_prev;
   const double mu4pi = periodic ? kFourPi * S.mu_sum * inv_n : 0.0;
   double acc = 0.0, ap_acc = 0.0, p_acc = 0.0;
+  if (project) {
 #pragma unroll 2
-  GRID_STRIDE(i, n) {
-    const double vi = project ? v[i] - c * s[i] : v[i];
-    double av = -qlam[i] * vi - kFourPi * r[i];
-    if (periodic) av += mu4pi * sqe[i];
-    const double pi_ = vi + beta * p[i];
-    const double api = av + beta * Ap[i];
-    p[i] = pi_;
-    Ap[i] = api;
-    acc += pi_ * api;
-    ap_acc += api;
-    p_acc += pi_;
+    GRID_STRIDE(i, n) {
+      const double vi = v[i] - c * s[i];
+      const double av = -qlam[i] * vi - kFourPi * r[i] + mu4pi * sqe[i];
+      const double pi_ = vi + beta * p[i];
+      const double api = av + beta * Ap[i];
+      p[i] = pi_;
+      Ap[i] = api;
+      acc += pi_ * api;
+      ap_acc += api;
+      p_acc += pi_;
+    }
+  } else if (periodic) {
+#pragma unroll 2
+    GRID_STRIDE(i, n) {
+      const double vi = v[i];
+      const double av = -qlam[i] * vi - kFourPi * r[i] + mu4pi * sqe[i];
+      const double pi_ = vi + beta * p[i];
+      const double api = av + beta * Ap[i];
+      p[i] = pi_;
+      Ap[i] = api;
+      acc += pi_ * api;
+    }
+  } else {
+    // free, surface and wire BC: five FP64 operations per point (the FP64
+    // pipe, not HBM, is the tighter bound of this kernel on GB300)
+#pragma unroll 2
+    GRID_STRIDE(i, n) {
+      const double vi = v[i];
+      const double av = -qlam[i] * vi - kFourPi * r[i];
+      const double pi_ = vi + beta * p[i];
+      const double api = av + beta * Ap[i];
+      p[i] = pi_;
+      Ap[i] = api;
+      acc += pi_ * api;
+    }
   }
   bool last;
   if (project)
@@ -374,14 +417,24 @@ __global__ void k_update_r(Batch b, Fields f, size_t n) {
   const double alpha = S.alpha;
   const double m = S.gauge ? S.ap_mean : 0.0;
   double acc = 0.0;
+  if (m != 0.0) {
 #pragma unroll 2
-  GRID_STRIDE(i, n) {
-    x[i] += alpha * p[i];
-    const double api = Ap[i] - m;
-    if (m != 0.0) Ap[i] = api;   // keep the projected A p for the recurrence
-    const double ri = r[i] - alpha * api;
-    r[i] = ri;
-    acc += ri * ri;
+    GRID_STRIDE(i, n) {
+      x[i] += alpha * p[i];
+      const double api = Ap[i] - m;
+      Ap[i] = api;   // keep the projected A p for the recurrence
+      const double ri = r[i] - alpha * api;
+      r[i] = ri;
+      acc += ri * ri;
+    }
+  } else {
+#pragma unroll 2
+    GRID_STRIDE(i, n) {
+      x[i] += alpha * p[i];
+      const double ri = r[i] - alpha * Ap[i];
+      r[i] = ri;
+      acc += ri * ri;
+    }
   }
   if (grid_reduce(acc, slot_partials(b, slot), &S.counter[CNT_RR], &S.rr) && threadIdx.x == 0) {
     S.pdone = 0;
@@ -396,7 +449,7 @@ __global__ void k_update_r(Batch b, Fields f, size_t n) {
     } else if (S.iter >= S.max_iter) {
       S.status = GPS_ERR_NOT_CONVERGED;
       after_pcg(S);
-    } else if (S.mixed && S.spec != SPEC_FP32 && S.rr <= S.mixed_switch * S.mixed_switch * S.rr0) {
+    } else if (S.mixed && S.spec != SPEC_FP32 && S.rr <= S.rr_switch) {
       S.spec = SPEC_FP32;
       S.rr_min = S.rr;
       S.stall = 0;
@@ -716,6 +769,15 @@ void launch_setup_final(const Batch& b, const Fields& f, size_t n, double inv_p,
 void launch_init(const Batch& b, const Fields& f, size_t n, int nslots, cudaStream_t st) {
   count_launch();
   k_init<<<VEC_GRID(n, nslots)>>>(b, f, n);
+}
+
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+  GRID_STRIDE(i, n) out[i] = d2f_rn(in[i]);
+}
+
+void launch_to_float(const double* in, float* out, size_t n, cudaStream_t st) {
+  count_launch();
+  k_to_float<<<grid_blocks(n, kT), kT, 0, st>>>(in, out, n);
 }
 
 void launch_update_p(const Batch& b, const Fields& f, size_t n, int periodic, int nslots,

@@ -30,6 +30,8 @@ struct Fields {
 
 int vec_blocks(size_t n, int nslots);
 void launch_setup_s(const Batch& b, const Fields& f, size_t n, int nslots, cudaStream_t st);
+// out = in rounded to float (round to nearest even), n values.
+void launch_to_float(const double* in, float* out, size_t n, cudaStream_t st);
 void launch_fd16_q(const Batch& b, const Fields& f, int nx, int ny, int nz, double hx, double hy,
                    double hz, int perx, int pery, int perz, const Fd16& c, int nslots,
                    cudaStream_t st);

@@ -91,6 +91,7 @@ _SIGS = {
                                         ctypes.POINTER(gps_electrolyte), _P, _P]),
     "gps_vacuum_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(gps_grid), _P, _P, _P]),
     "gps_set_radix_order": (ctypes.c_int, [ctypes.c_int]),
+    "gps_set_x_kernel": (ctypes.c_int, [ctypes.c_int]),
     "gps_sccs_eps": (ctypes.c_int, [_P, ctypes.c_size_t, _P, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, _P, _P, _P]),
     "gps_polarization_charge": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P, _P, _P]),
@@ -111,9 +112,11 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "gps_kernel_launches": (ctypes.c_ulonglong, []),
 }
-GPS_PROFILE_KINDS = 10
-PROFILE_KINDS = ["x_fwd", "y_fwd", "z", "y_inv", "x_inv", "update_p", "update_r", "other", "stencil",
-                 "sc_vector"]
+GPS_PROFILE_KINDS = 20
+_PASSES = ["x_fwd", "y_fwd", "z", "y_inv", "x_inv"]
+# kinds 0-4: passes of the FP64 spectrum; 10-14 double-float; 15-19 FP32
+PROFILE_KINDS = (_PASSES + ["update_p", "update_r", "other", "stencil", "sc_vector"]
+                 + [k + "_df64" for k in _PASSES] + [k + "_fp32" for k in _PASSES])
 
 _lib = None
 
@@ -328,6 +331,11 @@ class Context:
 def set_radix_order(order):
     """-1: tune the FFT radix order (default); 0..3: use that order for new plans."""
     _check(load().gps_set_radix_order(int(order)), "gps_set_radix_order")
+
+
+def set_x_kernel(kind):
+    """FP32 x passes: -1 tuned (default), 0 shared-memory kernels, 1 register-resident."""
+    _check(load().gps_set_x_kernel(int(kind)), "gps_set_x_kernel")
 
 
 def make_request(grid, kind, rho, eps, phi, electrolyte=None, opts=None):

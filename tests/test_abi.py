@@ -89,6 +89,9 @@ def test_new_defaults_and_host_side_argument_checks(lib):
     assert L.gps_set_radix_order(4) == gps.GPS_ERR_INVALID
     assert L.gps_set_radix_order(-2) == gps.GPS_ERR_INVALID
     assert L.gps_set_radix_order(-1) == gps.GPS_OK
+    assert L.gps_set_x_kernel(2) == gps.GPS_ERR_INVALID
+    assert L.gps_set_x_kernel(-2) == gps.GPS_ERR_INVALID
+    assert L.gps_set_x_kernel(-1) == gps.GPS_OK
     g = gps.gps_grid()
     rep = gps.gps_report()
     assert L.gps_gpe_solve(None, ctypes.byref(g), None, None, None, ctypes.byref(o), ctypes.byref(rep),

@@ -208,6 +208,28 @@ def test_precondition_column_kernels(gps, ctx, bc, n, h, prec, tol):
     assert relmax(N(v, g.shape), f.precondition(r)) < tol
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("bc,n,h", [c for c in COLUMN if c[1][0] >= 32])
+def test_precondition_fp32_x_kernels(gps, bc, n, h, kind):
+    """FP32 x passes by the shared-memory (0) and the register-resident (1)
+    kernels, whichever the tuner would pick: the preconditioner against the
+    oracle at the FP32 spectrum's tolerance."""
+    g = _grid(bc, n, h)
+    rng = np.random.default_rng(23)
+    eps = 1.0 + 30.0 * rng.random(g.shape)
+    r = rng.standard_normal(g.shape)
+    f = Fields(g, eps)
+    gps.set_x_kernel(kind)
+    c = gps.Context(0)
+    try:
+        v = T(np.zeros(g.shape))
+        c.precondition(gps.grid_from(g), T(f.s), T(r), v, precision=gps.GPS_MIXED)
+        assert relmax(N(v, g.shape), f.precondition(r)) < 2e-5
+    finally:
+        c.close()
+        gps.set_x_kernel(-1)
+
+
 def _has_solvent(p):
     """A slab test box must reach above the interface (z = 10 bohr): below it
     eps = 1 and the problem is vacuum Poisson."""

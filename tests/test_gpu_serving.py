@@ -172,6 +172,70 @@ def test_server_stream_identical_to_alone(gps, ctx):
     assert stats["max_concurrent"] >= 2
 
 
+def _bench_requests(gps, count=9, seed=1005):
+    """Requests drawn like the benchmark's serving stream (h = 0.3, edges 48,
+    64 and 96, every BC and problem), all on the mixed-precision path the
+    benchmark serves: double-float spectrum, FP32 after the switch, FP64
+    certificate; nonlinear PB included."""
+    rng = np.random.default_rng(seed)
+    out = []
+    kinds = ("gpe", "lpb", "nlpb")
+    for i in range(count):
+        edge = (48, 64, 96)[i % 3]
+        bc = int(rng.integers(0, 3))
+        kind = kinds[(i // 3) % 3]
+        p = synth.serving_request(rng, edge, bc, kind)
+        opts = gps.default_opts(tol_abs=1e-10, tol_outer=1e-10, max_iter=3000,
+                                precision=gps.GPS_MIXED_DF64)
+        el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, 300.0, p.eps0)
+        out.append((p, kind, opts, el))
+    return out
+
+
+def test_server_mixed_df64_stream_identical_to_alone(gps, ctx):
+    """The benchmark's serving configuration: every request (GPe, linear and
+    nonlinear PB, edges 48-96) on GPS_MIXED_DF64, arriving while others are on
+    the GPU, gives the bitwise result of its single solve, carries an FP64
+    certificate below 1e-8, and the smallest nonlinear one matches the
+    oracle's FP64 solution to 1e-8."""
+    reqs = _bench_requests(gps)
+    alone = _alone(gps, ctx, reqs)
+    srv = gps.Server(0, hbm_budget_bytes=16 << 30)
+    rng = np.random.default_rng(6)
+    tickets, keep = [], []
+
+    def producer():
+        for p, kind, opts, el in reqs:
+            rho = np.ascontiguousarray(p.rho.ravel())
+            eps = np.ascontiguousarray(p.eps.ravel())
+            phi = np.full(p.grid.npts, np.nan)
+            keep.append((rho, eps, phi))
+            r = gps.make_request(gps.grid_from(p.grid), kind, rho, eps, phi, el, opts)
+            tickets.append(srv.submit(r, keep=keep[-1]))
+            time.sleep(float(rng.exponential(0.02)))
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    results = [srv.wait(t) for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    for (phi_a, rep_a), (_, _, phi_b), (status, rep_b) in zip(alone, keep, results):
+        assert status == 0 and rep_a.status == 0
+        assert rep_a.iters == rep_b.iters
+        assert 0 <= rep_b.fixed_point_res < 1e-8
+        assert np.array_equal(phi_a, phi_b)
+    assert stats["max_concurrent"] >= 2
+    nl = [i for i, r in enumerate(reqs) if r[1] == "nlpb"]
+    i = min(nl, key=lambda k: reqs[k][0].grid.npts)
+    p = reqs[i][0]
+    ref, info = oracle.solve_nlpb(p.grid, p.rho, p.eps, p.electrolyte, p.eps0, tol=1e-11, max_iter=3000)
+    assert info["converged"]
+    got = keep[i][2].reshape(ref.shape)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= 1e-8, err
+
+
 def test_server_admission_under_budget(gps):
     """A budget that holds one small pool at a time still completes every
     request (pools are evicted when idle); a budget below one pool fails the
