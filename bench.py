@@ -1,21 +1,30 @@
-"""Benchmark: PCG generalized Poisson solve on the 128^3 periodic workload.
+"""Benchmark: nonlinear Poisson-Boltzmann solve of the free-BC 256^3 workload.
 
-One step = one complete solve through the C ABI (gps_gpe_solve): setup of
-s, sqrt(eps) and q, then Algorithm 2 to ||r||_2 <= 1e-10, FP64, inputs
-resident in HBM.  The metric is PCG grid-point iterations per second
-(grid points x PCG iterations / solve time), aggregated over ranks.
+One step = one complete solve through the C ABI (gps_pb_solve, kind NLPB):
+setup of s, sqrt(eps) and q, then the Newton outer loop of Algorithm 4 with
+Algorithm 2 inside, to an outer residual <= 1e-10, on the mixed-precision
+path (double-float spectrum, FP32 spectrum once ||r|| <= 1e-2 ||r_ref||,
+FP64 vectors, dot products and ionic term, FP64 certificate of the result),
+inputs resident in HBM.  Workload: free BC, 256^3 points at h = 0.3 bohr,
+200 Gaussian charges in a union-of-spheres cavity, 1:1 electrolyte at 0.5 M.
+The value is PCG grid-point iterations per second (grid points x PCG
+iterations / solve time) aggregated over ranks; solves/s, the plain FP64
+solve of the same problem (solves/s and the error of the mixed result
+against it) and the end-to-end rate through gps_pb_solve_host go beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle (the reference implementation of the
 method written for the tests) on the host cores, each step a bounded sample
-of the same workload: setup plus a fixed number of PCG iterations.
+of the same workload: setup plus a fixed number of PCG iterations of the
+first Newton step's inner solve.
 
 Under torchrun each rank solves its own replica of the workload on its own
 GPU (the solve does not shard; "replicas only"), timing is the max over
 ranks, and the value is the total over ranks.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -29,10 +38,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "gpe_periodic_128"
-METRIC = "PCG grid-pt*iter/s (GPe, periodic 128^3, FP64, ||r|| <= 1e-10)"
+WORKLOAD = "free_nlpb_256"
+METRIC = ("PCG grid-pt*iter/s, nonlinear PB (free 256^3, 200 charges, union of spheres, 0.5 M), "
+          "mixed precision certified <= 1e-8 (solves/s and the plain FP64 path beside it)")
 UNIT = "grid-pt*iter/s"
 L2_FLUSH_BYTES = 512 << 20
+TOL_OUTER = 1e-10
 
 
 def dist_env():
@@ -43,9 +54,16 @@ def dist_env():
 
 
 def config_dict(extra=None):
-    d = {"workload": WORKLOAD, "grid": [128, 128, 128], "h_bohr": 0.3, "bc": "periodic",
-         "charges": 20, "eps0": 78.36, "tol_abs": 1e-10, "problem": "generalized Poisson",
-         "l2_flush": "512 MiB buffer written between timed steps", "parallelism": "replicas"}
+    d = {"workload": WORKLOAD, "grid": [256, 256, 256], "h_bohr": 0.3, "bc": "free",
+         "charges": 200, "eps0": 78.36, "cavity": "union of erf spheres (d_i = 1.2 U[2.5, 3.5], Delta 0.5)",
+         "problem": "nonlinear PB (Eq. PBe), Newton outer loop of Algorithm 4 around Algorithm 2",
+         "electrolyte": "1:1, 0.5 mol/L, 300 K, ion exclusion = cavity function",
+         "tol_outer": TOL_OUTER,
+         "precision": "mixed: df64 spectrum, FP32 spectrum once ||r|| <= 1e-2 ||r_ref||; FP64 vectors, "
+                      "dots, alpha/beta and ionic term; FP64 certificate",
+         "l2_flush": "inputs larger than L2 (each FP64 field 134 MB) and a 512 MiB buffer written "
+                     "between timed steps",
+         "parallelism": "replicas"}
     if extra:
         d.update(extra)
     return d
@@ -106,15 +124,32 @@ def peaks():
         return {}
 
 
-# FP64 FMA units: 152 SMs x 2 DFMA/clk (measured 600 GFMA/s on this GPU) at
-# the 2070 MHz maximum SM clock, 2 flop per FMA.
+# FP64 FMA units: 152 SMs x 2 DFMA/clk (measured 600 GFMA/s on this GPU, see
+# --fp64-peak) at the 2070 MHz maximum SM clock, 2 flop per FMA.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel from one
+# ncu capture, valid only for the kernel source it was taken with (the SHA-256
+# of the listed files, first 16 hex digits); otherwise the line reports null.
+NCU_TRAFFIC = {}
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel on this workload, from the ncu capture summarized in
-# profiles/k_z_gpe_periodic_128.md (to be retaken whenever the kernel changes).
-NCU_TRAFFIC = {"z": 19335936}
+
+def source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1509_00680_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kind):
+    rec = NCU_TRAFFIC.get(kind)
+    if not rec:
+        return None
+    try:
+        return rec["bytes"] if source_sha(rec["files"]) == rec["sha"] else None
+    except OSError:
+        return None
 
 
 def pass_geometry(grid):
@@ -158,6 +193,19 @@ def reduce_over_ranks(total_ms, units, device=None):
     return float(tmax.item()), float(usum.item())
 
 
+def timed_call(stream, flush, fn):
+    """One call bracketed by CUDA events on `stream` after an L2 flush."""
+    import torch
+    flush.fill_(1.0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_1509_00680_gb300 import build
@@ -171,15 +219,17 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    p = synth.workload(2)
+    p = synth.workload(4)
     g = gps.grid_from(p.grid)
     npts = p.grid.npts
+    e = p.electrolyte
+    el = gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0)
     rho = torch.from_numpy(p.rho.ravel()).to(dev)
     eps = torch.from_numpy(p.eps.ravel()).to(dev)
-    phi = torch.empty_like(rho)
+    phi = torch.zeros_like(rho)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     ctx = gps.Context(local)
-    opts = gps.default_opts(tol_abs=1e-10)
+    opts = gps.default_opts(tol_outer=TOL_OUTER, max_iter=3000, precision=gps.GPS_MIXED_DF64)
     stream = torch.cuda.current_stream()
     P = pass_geometry(p.grid)
 
@@ -189,77 +239,90 @@ def run_ours(args, ws, rank, local):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up solves, timing every kernel kind to find the dominant one
-    ctx.set_profiling("all")
+    def solve(o, out):
+        out.zero_()
+        return ctx.pb_solve(g, rho, eps, el, "nlpb", out, o)
+
     for _ in range(args.warmup):
-        ctx.gpe_solve(g, rho, eps, phi, opts)
-    warm = {k: v for k, v in ctx.get_profile(reset=True).items() if v[0] > 0}
-    dom = max(warm, key=lambda k: warm[k][1])
-    shares = {k: round(v[1] / sum(w[1] for w in warm.values()), 4) for k, v in warm.items()}
+        solve(opts, phi)
     barrier()
     clocks = ClockSampler(local, args.clocks_log)
     clocks.start()
-    ctx.set_profiling([dom])             # only the dominant kernel is event-timed
-    ctx.get_profile(reset=True)
     launches0 = gps.kernel_launches()
-    t_steps, iters = [], []
+    t_steps, reps = [], []
     torch.cuda.profiler.start()               # ncu --profile-from-start off: timed steps only
     for _ in range(args.steps):
-        flush.fill_(1.0)                      # evict L2 between steps (not timed)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rep = ctx.gpe_solve(g, rho, eps, phi, opts)
-        e1.record(stream)
-        e1.synchronize()
-        t_steps.append(e0.elapsed_time(e1))
-        iters.append(rep.iters)
+        rep, ms = timed_call(stream, flush, lambda: solve(opts, phi))
+        t_steps.append(ms)
+        reps.append(rep)
     torch.cuda.profiler.stop()
     barrier()
     launches = gps.kernel_launches() - launches0
-    prof = ctx.get_profile(reset=True)
-    ctx.set_profiling(None)
     clk = clocks.stop()
+    iters = [r.iters for r in reps]
     total_ms, units = reduce_over_ranks(sum(t_steps), npts * sum(iters), dev)
+    _, solves = reduce_over_ranks(sum(t_steps), len(t_steps), dev)
     value = units / (total_ms / 1e3)
+    last = reps[-1]
+    headline = {"solves_per_s": solves / (total_ms / 1e3), "ms_per_solve": total_ms / args.steps,
+                "pcg_iters": int(statistics.median(iters)), "outer_iters": last.outer_iters,
+                "high_precision_iters": last.fp64_iters, "certificate": last.fixed_point_res,
+                "outer_res": last.outer_res, "status": last.status}
 
-    e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(ctx, g, p, npts, opts, flush, args)
-    mixed = None if args.no_mixed else run_mixed(ctx, g, rho, eps, phi, flush, args, gps, total_ms / args.steps)
-    df64 = None if args.no_mixed else run_mixed(ctx, g, rho, eps, phi, flush, args, gps, total_ms / args.steps,
-                                                precision=gps.GPS_DF64)
-    mixed_df64 = None if args.no_mixed else run_mixed(ctx, g, rho, eps, phi, flush, args, gps,
-                                                      total_ms / args.steps, precision=gps.GPS_MIXED_DF64)
-    warm = None if args.no_mixed else run_warm(gps, local, p, g, rho, eps, flush)
+    # the plain FP64 GPU path on the same problem (FP64 spectrum throughout)
+    fp64 = None
+    if not args.no_fp64:
+        phi64 = torch.zeros_like(rho)
+        o64 = gps.default_opts(tol_outer=TOL_OUTER, max_iter=3000, precision=gps.GPS_FP64)
+        rep64, ms64 = timed_call(stream, flush, lambda: solve(o64, phi64))
+        err = (torch.linalg.norm(phi - phi64) / torch.linalg.norm(phi64)).item()
+        fp64 = {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "pcg_iters": rep64.iters,
+                "outer_iters": rep64.outer_iters, "grid_pt_iter_per_s": npts * rep64.iters / (ms64 / 1e3),
+                "status": rep64.status, "timed_solves": 1,
+                "mixed_rel_l2_err_vs_fp64": err,
+                "mixed_speedup_solves_per_s": (1e3 / ms64) and headline["solves_per_s"] / (1e3 / ms64)}
+        del phi64
+
+    # kernel times: one more mixed solve, untimed, every kernel kind event-timed
+    ctx.set_profiling("all")
+    ctx.get_profile(reset=True)
+    solve(opts, torch.zeros_like(rho))
+    torch.cuda.synchronize()
+    prof = {k: v for k, v in ctx.get_profile(reset=True).items() if v[0] > 0}
+    ctx.set_profiling(None)
+    ktot = sum(v[1] for v in prof.values())
+    shares = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / ktot, 4)}
+              for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    dom = max(prof, key=lambda k: prof[k][1])
+    roof = kernel_roofline(dom, prof[dom][1] / prof[dom][0], P, peaks())
+    roof["kernel_time_shares"] = shares
+    roof["measured_in"] = "one untimed mixed solve after the timed steps, every kernel kind event-timed"
+    runner_up = {}
+    for k in sorted(prof, key=lambda k: -prof[k][1])[1:4]:
+        runner_up[k] = kernel_roofline(k, prof[k][1] / prof[k][0], P, peaks())
+    roof["next_kernels"] = runner_up
+
+    e2e = None if args.no_e2e else run_e2e(ctx, g, p, el, npts, opts, args)
+    ctx.close()
+    del phi
+    torch.cuda.empty_cache()
+    periodic128 = None if args.no_periodic128 else run_periodic128(gps, local, flush, args)
     nonlinear = None if args.no_nonlinear else run_nonlinear(gps, local, flush)
     comparison = None if args.no_comparison else run_comparison(gps, local, flush)
     wire = None if args.no_wire else run_wire(gps, local, flush)
     dft = None if args.no_dft else run_dft(gps, local, flush)
     serving = None if args.no_serving else run_serving(gps, local, args)
 
-    # roofline of the dominant kernel (largest share of kernel time in warm-up)
-    n_l, t_l = prof[dom]
-    avg_ms = t_l / max(n_l, 1)
-    fl = kernel_flops(dom, P)
-    ach = fl / (avg_ms / 1e3) / 1e12
-    roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(dom),
-            "avg_launch_ms": avg_ms, "launches_timed": n_l,
-            "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)",
-            "flops_model": "5 L log2 L per complex FFT of length L (+2 per point for the table)",
-            "kernel_time_shares_warmup": shares}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict({"pcg_iters_per_solve": int(statistics.median(iters))}),
-        "solves_per_s": ws * args.steps / (total_ms / 1e3),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+df64+f32", "data": "synthetic",
+        "config": config_dict({"pcg_iters_per_solve": headline["pcg_iters"]}),
+        "solves_per_s": headline["solves_per_s"],
+        "headline": headline,
+        "fp64": fp64,
         "e2e": e2e,
-        "mixed": mixed,
-        "df64": df64,
-        "mixed_df64": mixed_df64,
-        "warm_start": warm,
+        "periodic128": periodic128,
         "nonlinear": nonlinear,
         "comparison": comparison,
         "wire": wire,
@@ -273,10 +336,57 @@ def run_ours(args, ws, rank, local):
         out["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:
         print(json.dumps(out))
-    ctx.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_periodic128(gps, device, flush, args):
+    """The 128^3 periodic GPe workload (20 charges, ||r|| <= 1e-10): the plain
+    FP64 PCG timed over `steps` solves (no profiling in the timed region),
+    then the other spectrum precisions, the warm start and the roofline of
+    the FP64 path's dominant kernel from one more, untimed, profiled solve."""
+    import torch
+    import synth
+    p = synth.workload(2)
+    g = gps.grid_from(p.grid)
+    npts = p.grid.npts
+    rho = torch.from_numpy(p.rho.ravel()).to(device)
+    eps = torch.from_numpy(p.eps.ravel()).to(device)
+    phi = torch.empty_like(rho)
+    ctx = gps.Context(device)
+    opts = gps.default_opts(tol_abs=1e-10)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        ctx.gpe_solve(g, rho, eps, phi, opts)
+    ts, its = [], []
+    for _ in range(args.steps):
+        rep, ms = timed_call(stream, flush, lambda: ctx.gpe_solve(g, rho, eps, phi, opts))
+        ts.append(ms)
+        its.append(rep.iters)
+    fp64_ms = sum(ts) / len(ts)
+    ctx.set_profiling("all")
+    ctx.get_profile(reset=True)
+    ctx.gpe_solve(g, rho, eps, torch.empty_like(rho), opts)
+    torch.cuda.synchronize()
+    prof = {k: v for k, v in ctx.get_profile(reset=True).items() if v[0] > 0}
+    ctx.set_profiling(None)
+    dom = max(prof, key=lambda k: prof[k][1])
+    out = {"workload": p.name, "grid": [128, 128, 128], "bc": "periodic", "tol_abs": 1e-10,
+           "grid_pt_iter_per_s": npts * sum(its) / (sum(ts) / 1e3), "solves_per_s": 1e3 / fp64_ms,
+           "ms_per_solve": fp64_ms, "pcg_iters": int(statistics.median(its)),
+           "roofline": kernel_roofline(dom, prof[dom][1] / prof[dom][0], pass_geometry(p.grid), peaks(),
+                                       periodic=True)}
+    out["roofline"]["kernel_time_shares"] = {k: round(v[1] / sum(w[1] for w in prof.values()), 4)
+                                             for k, v in prof.items()}
+    if not args.no_mixed:
+        out["mixed"] = run_mixed(ctx, g, rho, eps, phi, flush, args, gps, fp64_ms)
+        out["df64"] = run_mixed(ctx, g, rho, eps, phi, flush, args, gps, fp64_ms, precision=gps.GPS_DF64)
+        out["mixed_df64"] = run_mixed(ctx, g, rho, eps, phi, flush, args, gps, fp64_ms,
+                                      precision=gps.GPS_MIXED_DF64)
+        out["warm_start"] = run_warm(gps, device, p, g, rho, eps, flush)
+    ctx.close()
+    return out
 
 
 def run_mixed(ctx, g, rho, eps, phi64, flush, args, gps, fp64_ms, precision=None):
@@ -343,13 +453,11 @@ def run_warm(gps, device, p, g, rho, eps, flush):
 
 
 def run_nonlinear(gps, device, flush):
-    """Nonlinear PB on the free-BC 256^3 union-of-spheres workload (200
-    Gaussians, 1:1 electrolyte at 0.5 M, 300 K): Eq. (PBe) with the Boltzmann
-    ionic charge, and the modified (steric) PB with p = 0.74 and R = 3
-    angstrom for both species, each by the Newton outer loop around
-    Algorithm 2 on the mixed-precision path (double-float spectrum, FP32 once
-    ||r|| <= 1e-2 ||r0||, FP64 certificate), outer tolerance 1e-10.  One
-    untimed solve per problem first (plans, tuning)."""
+    """Modified (steric) PB on the headline workload (free 256^3, 200
+    Gaussians, 1:1 electrolyte at 0.5 M, 300 K, p = 0.74 and R = 3 angstrom
+    for both species), by the Newton outer loop around Algorithm 2 on the
+    same mixed-precision path, outer tolerance 1e-10.  One untimed solve
+    first (plans, tuning)."""
     import torch
     import synth
     p = synth.workload(4)
@@ -357,29 +465,20 @@ def run_nonlinear(gps, device, flush):
     rho = torch.from_numpy(p.rho.ravel()).to(device)
     eps = torch.from_numpy(p.eps.ravel()).to(device)
     e = p.electrolyte
-    els = {"nlpb": ("nlpb", gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0)),
-           "mpb": ("mpb", gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0,
-                                               radius_angstrom=(3.0,) * len(e.z), packing=0.74))}
+    el = gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0, radius_angstrom=(3.0,) * len(e.z),
+                              packing=0.74)
     ctx = gps.Context(device)
     stream = torch.cuda.current_stream()
-    opts = gps.default_opts(tol_outer=1e-10, max_iter=3000, precision=gps.GPS_MIXED_DF64)
-    out = {"workload": p.name, "grid": list(p.grid.shape), "precision": "mixed_df64",
-           "steric": {"packing": 0.74, "radius_angstrom": 3.0}}
-    for name, (kind, el) in els.items():
-        phi = torch.zeros_like(rho)
-        ctx.pb_solve(g, rho, eps, el, kind, phi, opts)
-        phi.zero_()
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rep = ctx.pb_solve(g, rho, eps, el, kind, phi, opts)
-        e1.record(stream)
-        e1.synchronize()
-        out[name] = {"ms": e0.elapsed_time(e1), "status": rep.status, "outer_iters": rep.outer_iters,
-                     "pcg_iters": rep.iters, "fp64_iters": rep.fp64_iters,
-                     "outer_res": rep.outer_res, "fixed_point_res": rep.fixed_point_res}
+    opts = gps.default_opts(tol_outer=TOL_OUTER, max_iter=3000, precision=gps.GPS_MIXED_DF64)
+    phi = torch.zeros_like(rho)
+    ctx.pb_solve(g, rho, eps, el, "mpb", phi, opts)
+    phi.zero_()
+    rep, ms = timed_call(stream, flush, lambda: ctx.pb_solve(g, rho, eps, el, "mpb", phi, opts))
     ctx.close()
-    return out
+    return {"workload": p.name, "problem": "modified PB (steric, p = 0.74, R = 3 angstrom)",
+            "precision": "mixed_df64", "mpb": {"ms": ms, "status": rep.status, "outer_iters": rep.outer_iters,
+                                               "pcg_iters": rep.iters, "high_precision_iters": rep.fp64_iters,
+                                               "outer_res": rep.outer_res, "fixed_point_res": rep.fixed_point_res}}
 
 
 # FP64 pipe operations per grid point of the stencil kernels (gps_opts.method
@@ -563,18 +662,26 @@ def run_experiments(args):
     print(json.dumps(out))
 
 
-def run_serving(gps, device, args, count=None):
-    """Bounded sample of the serving workload: requests drawn like the
-    512-request stream (edges {48,64,96,128,192}, BC and problem mixed,
-    5-80 charges, 0.01-1 M), Poisson arrivals at 1.5x the capacity measured
-    by a batch solve of the same requests (then a second stream at 0.5x
-    capacity for the latency of a sustainable load), 120 GB admission budget.  Every
-    request runs the mixed-precision path (FP32 spectrum inside the FP64
-    PCG once ||r|| <= 1e-2 ||r0||, double-float spectrum before that, FP64
-    certificate of the result)."""
+def run_serving(gps, device, args):
+    """The serving workload: `--serving-count` requests (default the 512 of
+    the configuration) drawn like the request stream (edges {48,64,96,128,
+    192}, BC and problem mixed, 5-80 charges, 0.01-1 M), 120 GB admission
+    budget, every request on the mixed-precision path (df64 spectrum, FP32
+    once ||r|| <= 1e-2 ||r_ref||, FP64 certificate).
+      capacity      one batch solve of the first `--serving-capacity-count`
+                    requests (after one untimed batch of one request per
+                    distinct grid and problem: plans, tuning, graphs);
+      saturated     Poisson arrivals at 1.5x that capacity through the server:
+                    throughput and latency (queueing included);
+      low load      the first `--serving-low-count` requests at 0.5x capacity:
+                    latency of a sustainable load;
+      fp64 / mixed  the plain FP64 path (FP64 spectrum, one solve per call
+      sequential    through the host-array entry points, as a served request
+                    arrives) and the mixed path the same way, on every k-th
+                    request (a uniform sample of `--serving-fp64-sample`)."""
     import threading
     import synth
-    count = count or args.serving_count
+    count = args.serving_count
     desc = synth.serving_stream(count=count, seed=1005)
     reqs = []
     for edge, bc, kind, seed in desc:
@@ -582,33 +689,38 @@ def run_serving(gps, device, args, count=None):
         p = synth.serving_request(rng, edge, bc, kind)
         el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, 300.0, p.eps0)
         reqs.append((p, kind, el))
+    mixed_opts = lambda: gps.default_opts(tol_abs=1e-10, tol_outer=1e-10, max_iter=3000,
+                                          precision=gps.GPS_MIXED_DF64)
 
-    def make(i):
+    def make(i, opts):
         p, kind, el = reqs[i]
         rho = np.ascontiguousarray(p.rho.ravel())
         eps = np.ascontiguousarray(p.eps.ravel())
         phi = np.zeros(p.grid.npts)
-        r = gps.make_request(gps.grid_from(p.grid), kind, rho, eps, phi, el,
-                             gps.default_opts(tol_abs=1e-10, tol_outer=1e-10, max_iter=3000,
-                                              precision=gps.GPS_MIXED_DF64))
+        r = gps.make_request(gps.grid_from(p.grid), kind, rho, eps, phi, el, opts)
         return r, (rho, eps, phi)
 
-    ctx = gps.Context(device, 120 << 30)
-    made = [make(i) for i in range(count)]
-    gps.batch_solve(ctx, [m[0] for m in made], allow=(0, 3))       # warm-up: plans, graphs
+    made = [make(i, mixed_opts()) for i in range(count)]
+    first = {}
+    for i, (edge, bc, kind, _) in enumerate(desc):
+        first.setdefault((edge, bc, kind), i)
+    budget = 120 << 30
+    ctx = gps.Context(device, budget)
+    gps.batch_solve(ctx, [made[i][0] for i in first.values()], allow=(0, 3))    # plans, graphs
+    ncap = min(count, args.serving_capacity_count)
     t0 = time.perf_counter()
-    gps.batch_solve(ctx, [m[0] for m in made], allow=(0, 3))
-    capacity = count / (time.perf_counter() - t0)
+    reps_b = gps.batch_solve(ctx, [m[0] for m in made[:ncap]], allow=(0, 3))
+    capacity = ncap / (time.perf_counter() - t0)
     ctx.close()
 
-    def stream(rate, seed):
-        srv = gps.Server(device, hbm_budget_bytes=120 << 30)
+    def stream(n, rate, seed):
+        srv = gps.Server(device, hbm_budget_bytes=budget)
         rng = np.random.default_rng(seed)
         tickets, keep = [], []
         start = time.perf_counter()
 
         def producer():
-            for i in range(count):
+            for i in range(n):
                 r, hold = made[i]
                 keep.append(hold)
                 tickets.append(srv.submit(r, keep=hold))
@@ -623,89 +735,191 @@ def run_serving(gps, device, args, count=None):
         srv.close()
         return results, wall, stats
 
-    # saturated (arrivals at 1.5x capacity): throughput; latencies include queueing
     rate = 1.5 * capacity
-    results, wall, stats = stream(rate, 77)
+    results, wall, stats = stream(count, rate, 77)
     lat = sorted(rep.time_ms for _, rep in results)
-    ok = sum(1 for s, _ in results if s == 0)
-    # low load (0.5x capacity): latency of a served request
-    res_l, wall_l, _ = stream(0.5 * capacity, 78)
+    ok = sum(1 for st_, _ in results if st_ == 0)
+    nlow = min(count, args.serving_low_count)
+    res_l, wall_l, _ = stream(nlow, 0.5 * capacity, 78)
     lat_l = sorted(rep.time_ms for _, rep in res_l)
-    return {"requests": count, "ok": ok, "arrival_rate_per_s": rate, "batch_capacity_solves_per_s": capacity,
-            "solves_per_s": count / wall, "p50_ms": float(np.percentile(lat, 50)),
+
+    # sequential single solves on a uniform sample: plain FP64, then mixed
+    k = max(1, count // max(1, args.serving_fp64_sample))
+    sample = list(range(0, count, k))
+    seq = {}
+    ctx = gps.Context(device, budget)
+    for name, prec in (("fp64", gps.GPS_FP64), ("mixed_df64", gps.GPS_MIXED_DF64)):
+        for i in sorted({(desc[j][0], desc[j][1], desc[j][2]): j for j in sample}.values()):
+            run_single(gps, ctx, reqs[i], prec)                      # plans and tuning, untimed
+        t0 = time.perf_counter()
+        st_ok = 0
+        for i in sample:
+            st_ok += run_single(gps, ctx, reqs[i], prec) == 0
+        dt = time.perf_counter() - t0
+        seq[name] = {"solves_per_s": len(sample) / dt, "ok": st_ok}
+    ctx.close()
+    served = count / wall
+    return {"requests": count, "ok": ok, "hbm_budget_bytes": budget,
+            "arrival_rate_per_s": rate, "batch_capacity_solves_per_s": capacity,
+            "batch_capacity_requests": ncap, "batch_ok": sum(1 for r in reps_b if r.status == 0),
+            "solves_per_s": served, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)),
-            "at_0.5x_capacity": {"arrival_rate_per_s": 0.5 * capacity, "solves_per_s": count / wall_l,
+            "at_0.5x_capacity": {"requests": nlow, "arrival_rate_per_s": 0.5 * capacity,
+                                 "solves_per_s": nlow / wall_l,
                                  "p50_ms": float(np.percentile(lat_l, 50)),
                                  "p99_ms": float(np.percentile(lat_l, 99)),
-                                 "ok": sum(1 for s, _ in res_l if s == 0)},
+                                 "ok": sum(1 for st_, _ in res_l if st_ == 0)},
+            "sequential": {"sample": "every %d-th request (%d of %d), one solve per call through the "
+                                     "host-array entry points" % (k, len(sample), count),
+                           "fp64_solves_per_s": seq["fp64"]["solves_per_s"],
+                           "mixed_df64_solves_per_s": seq["mixed_df64"]["solves_per_s"],
+                           "ok": {n: v["ok"] for n, v in seq.items()}},
+            "served_vs_fp64_sequential": served / seq["fp64"]["solves_per_s"],
             "max_concurrent": stats["max_concurrent"],
-            "pool_bytes": stats["bytes_in_use"], "precision": "mixed_df64 (FP32 spectrum after the switch, df64 before, FP64 certificate)",
+            "pool_bytes": stats["bytes_in_use"],
+            "precision": "mixed_df64 (FP32 spectrum after the switch, df64 before, FP64 certificate)",
             "max_certificate": float(max(rep.fixed_point_res for _, rep in results))}
 
 
-def run_e2e(ctx, g, p, npts, opts, flush, args):
-    """Same metric through the host-pointer entry point: the H2D copy of rho
-    and eps from pinned memory and the D2H copy of phi are inside the timed
-    region of every step."""
+def run_single(gps, ctx, req, precision):
+    """One serving request solved alone through the host-array entry point."""
+    p, kind, el = req
+    rho = np.ascontiguousarray(p.rho.ravel())
+    eps = np.ascontiguousarray(p.eps.ravel())
+    phi = np.zeros(p.grid.npts)
+    o = gps.default_opts(tol_abs=1e-10, tol_outer=1e-10, max_iter=3000, precision=precision)
+    g = gps.grid_from(p.grid)
+    if kind == "gpe":
+        return ctx.gpe_solve_host(g, rho, eps, phi, o).status
+    return ctx.pb_solve_host(g, rho, eps, el, kind, phi, o, allow=(0, 3)).status
+
+
+def run_e2e(ctx, g, p, el, npts, opts, args):
+    """Same metric through the host-pointer entry point gps_pb_solve_host:
+    the H2D copy of rho and eps from pinned memory and the D2H copy of phi
+    are inside the timed region of every step (wall clock around the call,
+    which returns after its stream synchronizes)."""
     import torch
     rho_h = torch.from_numpy(p.rho.ravel().copy()).pin_memory().numpy()
     eps_h = torch.from_numpy(p.eps.ravel().copy()).pin_memory().numpy()
     phi_h = torch.empty(npts, dtype=torch.float64).pin_memory().numpy()
-    ctx.gpe_solve_host(g, rho_h, eps_h, phi_h, opts)
-    e2e_ms, e2e_iters = 0.0, 0
-    for _ in range(max(3, args.steps // 2)):
-        flush.fill_(1.0)
+    e2e_ms, e2e_iters, n = 0.0, 0, max(2, args.e2e_steps)
+    for _ in range(n):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rep = ctx.gpe_solve_host(g, rho_h, eps_h, phi_h, opts)
+        rep = ctx.pb_solve_host(g, rho_h, eps_h, el, "nlpb", phi_h, opts)
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_iters += rep.iters
-    return {"value": npts * e2e_iters / (e2e_ms / 1e3), "unit": UNIT,
+    return {"value": npts * e2e_iters / (e2e_ms / 1e3), "unit": UNIT, "steps": n,
+            "solves_per_s": n / (e2e_ms / 1e3),
             "h2d_bytes_per_step": 2 * npts * 8, "d2h_bytes_per_step": npts * 8}
 
 
 def oracle_sample(p, iters):
-    """Setup plus `iters` PCG iterations of the oracle on the workload; returns
-    (seconds, iterations)."""
+    """Setup plus `iters` PCG iterations of the oracle on the headline
+    workload: the first Newton step of Algorithm 4 (ionic charge and its
+    derivative at phi = 0, the linearized operator, Algorithm 2 on the
+    outer residual); returns (seconds, iterations)."""
     import oracle
     from oracle.operators import Fields
-    from oracle.pcg import neutralize, pcg
+    from oracle.pcg import pcg
     t0 = time.perf_counter()
-    f = Fields(p.grid, p.eps)
-    rho, _ = neutralize(p.rho, p.grid)
-    _, info = pcg(f, rho, tol_abs=1e-10, max_iter=iters)
+    e = p.electrolyte
+    gam = oracle.pb.exclusion_from_eps(p.eps, p.eps0)
+    phi = np.zeros_like(p.rho)
+    lam = -4.0 * np.pi * oracle.pb.ionic_charge_derivative(phi, gam, e)
+    f = Fields(p.grid, p.eps, lam=lam)
+    # first outer step: rho_ions = rho_ions[0] = fresh, r' = rho, so the inner
+    # source rho + fresh - rho_ions is rho itself (free BC: no background)
+    _, info = pcg(f, p.rho, tol_abs=0.0, tol_rel=1e-13, max_iter=iters)
     return time.perf_counter() - t0, info["iters"]
 
 
-def cpu_baseline(p, iters=40):
+def cpu_baseline(p, iters=8):
     secs, it = oracle_sample(p, iters)
     return {"value": p.grid.npts * it / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "oracle setup + %d PCG iterations of the 128^3 periodic workload (%.1f s)" % (it, secs)}
+            "sample": "oracle setup (Green's table, s, q, ionic terms) + %d PCG iterations of the first "
+                      "Newton step of the free 256^3 nonlinear-PB workload (%.1f s)" % (it, secs)}
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
     import synth
-    p = synth.workload(2)
-    iters = 8
+    p = synth.workload(4)
+    iters = 4
     for _ in range(args.warmup):
-        oracle_sample(p, 2)
+        oracle_sample(p, 1)
     secs, its = 0.0, 0
     for _ in range(args.steps):
-        s, i = oracle_sample(p, iters)
-        secs += s
+        sec, i = oracle_sample(p, iters)
+        secs += sec
         its += i
     value = p.grid.npts * its / secs
-    sample = "per step: oracle setup + %d PCG iterations of the 128^3 periodic workload" % iters
+    sample = ("per step: oracle setup + %d PCG iterations of the first Newton step of the free 256^3 "
+              "nonlinear-PB workload" % iters)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": config_dict(),
+           "data": "synthetic", "config": config_dict({"precision": "FP64 (oracle)"}),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def run_cpu_configs(args):
+    """The CPU oracle on each configuration's workload, median of 5 timed runs
+    after 1 warm-up: setup plus a fixed number of PCG iterations (configs 3
+    and 4: of the first Newton step of the nonlinear problem), as grid-pt*iter/s
+    and the implied seconds per PCG iteration."""
+    import synth
+    cases = [("1 gpe_free_64", synth.workload(1), 10, False),
+             ("2 gpe_periodic_128", synth.workload(2), 10, False),
+             ("3 surface_nlpb_160x160x256", synth.workload(3, kind="nlpb"), 6, True),
+             ("4 free_nlpb_256", synth.workload(4), 4, True)]
+    out = {"cores": os.cpu_count(), "kind": "oracle", "configs": {}}
+    for name, p, iters, nl in cases:
+        fn = (lambda: oracle_sample(p, iters)) if nl else (lambda: gpe_oracle_sample(p, iters))
+        fn()
+        runs = [fn() for _ in range(5)]
+        secs = statistics.median(r[0] for r in runs)
+        its = runs[0][1]
+        out["configs"][name] = {"grid_pt_iter_per_s": p.grid.npts * its / secs, "seconds": secs,
+                                "iters": its, "sample": "setup + %d PCG iterations" % its}
+    print(json.dumps(out))
+
+
+def gpe_oracle_sample(p, iters):
+    from oracle.operators import Fields
+    from oracle.pcg import neutralize, pcg
+    t0 = time.perf_counter()
+    f = Fields(p.grid, p.eps)
+    rho, _ = neutralize(p.rho, p.grid)
+    _, info = pcg(f, rho, tol_abs=0.0, tol_rel=1e-13, max_iter=iters)
+    return time.perf_counter() - t0, info["iters"]
+
+
+def run_fp64_peak(args):
+    """Measured FP64 rate of this GPU: a cuBLAS DGEMM (torch.matmul, FP64,
+    8192^3, 2 N^3 flops, best of 5 after 2 warm-ups), for comparison with
+    the derived FP64-pipe peak used by the roofline."""
+    import torch
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        torch.matmul(a, b)
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    print(json.dumps({"fp64_dgemm_tflops": 2 * n ** 3 / (best / 1e3) / 1e12, "n": n, "best_ms": best,
+                      "derived_fp64_pipe_tflops": FP64_PEAK_TFLOPS}))
 
 
 PASS_CASES = {
@@ -719,15 +933,55 @@ PASS_CASES = {
 
 def pass_bytes(P, e):
     """Algorithmic HBM bytes of each spectrum pass of one preconditioner
-    application: FP64 input r and factor s, spectrum elements of e bytes
-    (only the planes and rows that hold data are read or written), the
-    octant table in FP64, FP64 output v and factor s."""
+    application with spectrum elements of e bytes (8 FP32, 16 FP64 or df64):
+    the x forward pass reads r (FP64) and s (FP32 copy on the FP32 path,
+    FP64 otherwise) and writes the half spectrum (only the planes and rows
+    that hold data); y and z passes read and write spectrum elements (z also
+    the octant Green's table, FP32 or FP64); the x inverse pass reads the half
+    spectrum, s and r (for (v, r)) and writes v (FP64)."""
     n = P["nx"] * P["ny"] * P["nz"]
+    se = 4 if e == 8 else 8
     half = P["nz"] * P["ny"] * P["Hx"] * e
     full = P["nz"] * P["Py"] * P["Hx"] * e
-    table = P["Hx"] * (P["Py"] // 2 + 1) * (P["Pz"] // 2 + 1) * 8
-    return {"x_fwd": 16 * n + half, "y_fwd": half + full, "z": 2 * full + table,
-            "y_inv": full + half, "x_inv": half + 16 * n}
+    table = P["Hx"] * (P["Py"] // 2 + 1) * (P["Pz"] // 2 + 1) * (4 if e == 8 else 8)
+    return {"x_fwd": (8 + se) * n + half, "y_fwd": half + full, "z": 2 * full + table,
+            "y_inv": full + half, "x_inv": half + (16 + se) * n}
+
+
+def vector_bytes(P, periodic=False):
+    """Algorithmic bytes of the PCG vector updates per launch (FP64 fields):
+    update_p reads v, r, q + lambda, p, A p and writes p, A p (periodic: also
+    sqrt(eps) and s); update_r reads phi, r, p, A p and writes phi, r."""
+    n = P["nx"] * P["ny"] * P["nz"]
+    return {"update_p": (72 if periodic else 56) * n, "update_r": 48 * n}
+
+
+def kernel_roofline(kind, ms, P, peaks_, periodic=False):
+    """Roofline entry of one kernel kind from its average launch time."""
+    hbm = peaks_.get("hbm_gbs")
+    prec = "fp64"
+    base = kind
+    for suf in ("_df64", "_fp32"):
+        if kind.endswith(suf):
+            base, prec = kind[:-len(suf)], suf[1:]
+    if base in ("x_fwd", "y_fwd", "z", "y_inv", "x_inv") and prec == "fp64":
+        fl = kernel_flops(base, P)
+        ach = fl / (ms / 1e3) / 1e12
+        return {"kernel": kind, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": ncu_traffic(kind),
+                "avg_launch_ms": ms,
+                "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe, measured by --fp64-peak)",
+                "flops_model": "5 L log2 L per complex FFT of length L (+2 per point for the table)"}
+    if base in ("x_fwd", "y_fwd", "z", "y_inv", "x_inv"):
+        byt = pass_bytes(P, 8 if prec == "fp32" else 16)[base]
+    else:
+        byt = vector_bytes(P, periodic).get(base)
+    if byt is None or not hbm:
+        return {"kernel": kind, "avg_launch_ms": ms}
+    ach = byt / (ms / 1e3) / 1e9
+    return {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "traffic": ncu_traffic(kind), "avg_launch_ms": ms,
+            "algorithmic_bytes": byt, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), burst"}
 
 
 def run_passes(args):
@@ -768,9 +1022,12 @@ def run_passes(args):
         ctx.set_profiling(None)
         byt = pass_bytes(P, e)
         res, tot = {}, 0.0
+        suf = "" if name == "fp64" else "_" + name
         for k, (cnt, ms) in prof.items():
             if not cnt:
                 continue
+            if suf and k.endswith(suf):
+                k = k[:-len(suf)]
             t = ms / cnt
             tot += t
             res[k] = {"us": round(t * 1e3, 2), "bytes": byt.get(k)}
@@ -836,18 +1093,33 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-nonlinear", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 solve of the headline")
+    ap.add_argument("--no-periodic128", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-comparison", action="store_true")
     ap.add_argument("--no-wire", action="store_true")
     ap.add_argument("--no-dft", action="store_true")
     ap.add_argument("--clocks-log", default=None, help="keep the nvidia-smi samples of the timed region here")
-    ap.add_argument("--serving-count", type=int, default=24)
+    ap.add_argument("--serving-count", type=int, default=512)
+    ap.add_argument("--serving-capacity-count", type=int, default=128)
+    ap.add_argument("--serving-low-count", type=int, default=48)
+    ap.add_argument("--serving-fp64-sample", type=int, default=32)
     ap.add_argument("--passes", default=None, choices=sorted(PASS_CASES),
                     help="per-pass times of one preconditioner application instead of the bench")
     ap.add_argument("--precisions", default="fp64,df64,fp32")
     ap.add_argument("--experiments", action="store_true",
                     help="the paper's GPe convergence experiment (accuracy vs iterations) instead of the bench")
     ap.add_argument("--exp-n", type=int, default=300, help="grid points per side of --experiments")
+    ap.add_argument("--fp64-peak", action="store_true", help="measure the FP64 rate (cuBLAS DGEMM)")
+    ap.add_argument("--cpu-configs", action="store_true",
+                    help="time the CPU oracle on every configuration (median of 5)")
     args = ap.parse_args()
+    if args.fp64_peak:
+        run_fp64_peak(args)
+        return
+    if args.cpu_configs:
+        run_cpu_configs(args)
+        return
     if args.passes:
         run_passes(args)
         return
