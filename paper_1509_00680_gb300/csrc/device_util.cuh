@@ -9,13 +9,15 @@
 namespace gps {
 
 // Double-float number: the unevaluated sum hi + lo of two floats, about 48
-// significant bits (|lo| <= ulp(hi)/2 after a product; a few ulps after a
-// chain of additions, see operator+).  Arithmetic by error-free
-// transformations (Knuth's TwoSum, FMA-based TwoProd, Dekker's renormalizing
-// Fast2Sum) runs on the FP32 pipe, which on this GPU issues 64x the FP64
-// rate.  Addition uses the "sloppy" two-sum form: its error is bounded by
-// u^2 (|a| + |b|) (u = 2^-24) up to a small factor, the norm-wise bound an
-// FFT's error analysis needs.
+// significant bits.  Arithmetic by error-free transformations (Knuth's
+// TwoSum, FMA-based TwoProd; Dekker's renormalizing Fast2Sum where a
+// normalized value is wanted) runs on the FP32 pipe, which on this GPU
+// issues 64x the FP64 rate.  Neither addition nor multiplication
+// renormalizes its result: hi is the rounded result of the hi parts and lo
+// collects the exact error terms, so each operation's error stays bounded by
+// a small multiple of u^2 (|a| + |b|) or u^2 |a||b| (u = 2^-24), the
+// norm-wise bound an FFT's error analysis needs, while |lo| may reach a few
+// ulps of hi along a chain of butterflies.
 using ::fma;
 
 struct df {
@@ -34,12 +36,10 @@ __device__ __forceinline__ df fast_two_sum(float a, float b) {   // |a| >= |b|
 }
 // Addition without the final renormalization: the TwoSum of the hi parts is
 // exact for any operands, so hi + lo stays the sum to within the rounding of
-// the lo parts; lo may exceed half an ulp of hi until the next product (or an
-// explicit fast_two_sum) renormalizes it.  In the FFT passes an element
-// goes through a few additions between two products (three per radix-8
-// butterfly; the elements that take no twiddle carry over a few stages), so
-// lo grows by a few ulps of hi and the norm-wise error bound keeps its u^2
-// order (tested: df64 spectra match the FP64 oracle to 1e-12).
+// the lo parts.  In the FFT passes an element goes through a few additions
+// and at most one product per stage, so lo grows by a few ulps of hi and the
+// norm-wise error bound keeps its u^2 order (tested: df64 spectra match the
+// FP64 oracle to 1e-12).
 __device__ __forceinline__ df operator+(df a, df b) {
   const float s = a.hi + b.hi;
   const float bb = s - a.hi;
@@ -48,12 +48,35 @@ __device__ __forceinline__ df operator+(df a, df b) {
 }
 __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+// Product without the final renormalization, like operator+: hi is the
+// rounded product of the hi parts, lo its exact TwoProd error plus the cross
+// terms, so hi + lo is the product to within u^2 |a||b| while lo may exceed
+// half an ulp of hi (by the few ulps that a chain of butterflies adds).
 __device__ __forceinline__ df operator*(df a, df b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);                     // TwoProd error
   e = fmaf(a.hi, b.lo, e);
   e = fmaf(a.lo, b.hi, e);
-  return fast_two_sum(p, e);
+  return df(p, e);
+}
+// a b + s c d (s = +1 or -1) as one double-float: the TwoSum of the two hi
+// products, their TwoProd errors and the four cross terms accumulated in the
+// low part (16 FP32 operations against 22 for two products and a sum).
+template <int S>
+__device__ __forceinline__ df df_dot2(df a, df b, df c, df d) {
+  const float p = a.hi * b.hi;
+  const float q = S > 0 ? c.hi * d.hi : -(c.hi * d.hi);
+  const float e1 = fmaf(a.hi, b.hi, -p);
+  const float e2 = S > 0 ? fmaf(c.hi, d.hi, -q) : fmaf(-c.hi, d.hi, -q);
+  const float s = p + q;
+  const float bb = s - p;
+  float lo = (p - (s - bb)) + (q - bb);                // TwoSum error of p + q
+  lo += e1 + e2;
+  lo = fmaf(a.hi, b.lo, lo);
+  lo = fmaf(a.lo, b.hi, lo);
+  lo = S > 0 ? fmaf(c.hi, d.lo, lo) : fmaf(-c.hi, d.lo, lo);
+  lo = S > 0 ? fmaf(c.lo, d.hi, lo) : fmaf(-c.lo, d.hi, lo);
+  return df(s, lo);
 }
 __device__ __forceinline__ df fma(df a, df b, df c) { return a * b + c; }
 
@@ -134,6 +157,13 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
 // a * conj(b)
 template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
   return mk<V>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+// double-float complex products: each component one two-product sum
+template <> __device__ __forceinline__ dfc cmul<dfc>(dfc a, dfc b) {
+  return mk<dfc>(df_dot2<-1>(a.x, b.x, a.y, b.y), df_dot2<+1>(a.x, b.y, a.y, b.x));
+}
+template <> __device__ __forceinline__ dfc cmulc<dfc>(dfc a, dfc b) {
+  return mk<dfc>(df_dot2<+1>(a.x, b.x, a.y, b.y), df_dot2<-1>(a.y, b.x, a.x, b.y));
 }
 
 // Sum of v over the block (any blockDim.x multiple of 32, <= 1024); result
