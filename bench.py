@@ -995,6 +995,8 @@ def run_passes(args):
     build.build()
     from paper_1509_00680_gb300 import gps
     nx, ny, nz, bc = PASS_CASES[args.passes]
+    gps.set_x_kernel(args.x_kernel)
+    gps.set_z_kernel(args.z_kernel)
     origin = (0.0, 0.0, 0.0)
     grid = synth.Grid(nx, ny, nz, 0.3, 0.3, 0.3, bc, origin=origin)
     g = gps.grid_from(grid)
@@ -1008,7 +1010,7 @@ def run_passes(args):
     peak = peaks().get("hbm_gbs")
     codes = {"fp64": (gps.GPS_FP64, 16), "fp32": (gps.GPS_MIXED, 8), "df64": (gps.GPS_DF64, 16)}
     out = {"passes": args.passes, "grid": [nx, ny, nz], "bc": bc, "P": [P["Px"], P["Py"], P["Pz"]],
-           "hbm_peak_gbs": peak}
+           "hbm_peak_gbs": peak, "x_kernel": args.x_kernel, "z_kernel": args.z_kernel}
     for name in args.precisions.split(","):
         code, e = codes[name]
         for _ in range(3):
@@ -1107,6 +1109,10 @@ def main():
     ap.add_argument("--passes", default=None, choices=sorted(PASS_CASES),
                     help="per-pass times of one preconditioner application instead of the bench")
     ap.add_argument("--precisions", default="fp64,df64,fp32")
+    ap.add_argument("--x-kernel", type=int, default=-1, choices=(-1, 0, 1),
+                    help="--passes: FP32 x-pass kernels (-1 tuned, 0 shared-memory, 1 register-resident)")
+    ap.add_argument("--z-kernel", type=int, default=-1, choices=(-1, 0, 1),
+                    help="--passes: FP32 / df64 z-pass kernel (-1 tuned, 0 plain, 1 TMA-staged)")
     ap.add_argument("--experiments", action="store_true",
                     help="the paper's GPe convergence experiment (accuracy vs iterations) instead of the bench")
     ap.add_argument("--exp-n", type=int, default=300, help="grid points per side of --experiments")

@@ -363,11 +363,12 @@ void gps_server_destroy(gps_server* srv);
  * Supported: GPS_BC_PERIODIC and GPS_BC_SURFACE grids whose padded FFT
  * lengths (nx, ny, and nz periodic or 2 nz surface) are even, at most 4096
  * and factor into 2, 3 and 5, and for which
- *     16 (nx + ny + Pz) + 8 (nx/2+1)(ny/2+1)(Pz/2+1) + 16 (nx/2+1) ny nz
- * bytes (twiddles, Green's-function octant table, spectrum; each of the
- * first four parts rounded up to 256 bytes) fit in the 8 MiB (8,388,608
- * byte) array.  The largest cubic periodic grid is 96^3 (8,171,264 bytes);
- * 96 x 96 x 100 and 100^3 are over the limit.  Anything else returns
+ *     16 (nx + ny + Pz) + 8 (nx/2+1)(ny/2+1)(Pz/2+1) + 16 Hp ny nz
+ * bytes, Hp = nx/2+1 rounded up to even (twiddles, Green's-function octant
+ * table, spectrum with an even row pitch; each of the first four parts
+ * rounded up to 256 bytes) fit in the 8 MiB (8,388,608 byte) array.  The
+ * largest cubic periodic grid is 96^3 (8,318,720 bytes); 96 x 96 x 100 and
+ * 100^3 are over the limit.  Anything else returns
  * GPS_ERR_INVALID.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current) and keeps it for the life of the
@@ -416,6 +417,16 @@ int gps_set_radix_order(int order);
  * register-resident ones where the length allows.  Clears the process-wide
  * tuning cache like gps_set_radix_order. */
 int gps_set_x_kernel(int kind);
+
+/* Kernel of the z pass of the FP32 and double-float spectra, for
+ * reproducible plans and for tests of both: -1 (the default) the tuner times
+ * the register-resident column kernel against its TMA-staged form (column
+ * tiles moved to shared memory by tensor copies, double-buffered in a
+ * persistent CTA; padded lengths 64 .. 1024) and keeps the faster; 0 always
+ * the plain kernel; 1 the TMA-staged one where it applies.  A bounded wait
+ * of the TMA-staged kernel that gives up makes the call return
+ * GPS_ERR_TIMEOUT.  Clears the process-wide tuning cache. */
+int gps_set_z_kernel(int kind);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 unsigned long long gps_kernel_launches(void);

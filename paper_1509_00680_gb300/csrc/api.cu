@@ -367,7 +367,7 @@ void timed(int kind, const Batch& b, cudaStream_t st, F&& launch) {
 struct Shape {
   gps_grid grid;
   size_t n = 0;
-  int Px = 0, Py = 0, Pz = 0, Hx = 0;
+  int Px = 0, Py = 0, Pz = 0, Hx = 0, Hp = 0;
   int periodic = 0;
   double inv_p = 0.0;
   PassGeom g;                 // heuristic geometry (reduction sizing)
@@ -520,12 +520,13 @@ std::shared_ptr<Shape> build_shape(const gps_grid* gr, cudaStream_t st) {
   S->Py = fx ? 2 * gr->ny : gr->ny;
   S->Pz = fz ? 2 * gr->nz : gr->nz;
   S->Hx = S->Px / 2 + 1;
+  S->Hp = spectrum_pitch(S->Hx);
   S->n = (size_t)gr->nx * gr->ny * gr->nz;
   S->periodic = gr->bc == GPS_BC_PERIODIC;
   S->inv_p = 1.0 / ((double)S->Px * S->Py * S->Pz);
   PassGeom& g = S->g;
   g.nx = gr->nx; g.ny = gr->ny; g.nz = gr->nz;
-  g.Px = S->Px; g.Py = S->Py; g.Pz = S->Pz; g.Hx = S->Hx;
+  g.Px = S->Px; g.Py = S->Py; g.Pz = S->Pz; g.Hx = S->Hx; g.Hp = S->Hp;
   g.nrows = gr->ny * gr->nz;
   g.lines_x = batch_lines(S->Px, (g.nrows + 1) / 2);
   g.tile_y = batch_lines(S->Py, S->Hx * gr->nz);
@@ -639,7 +640,7 @@ struct Pool {
 };
 
 size_t slot_bytes(const Shape& S) {
-  const size_t wn = (size_t)S.Hx * S.Py * S.grid.nz;
+  const size_t wn = (size_t)S.Hp * S.Py * S.grid.nz;
   return 18 * S.n * sizeof(double) + S.n * sizeof(float) + wn * (sizeof(double2) + sizeof(float2)) +
          3 * 4096 * sizeof(double);
 }
@@ -649,7 +650,7 @@ std::unique_ptr<Pool> make_pool(std::shared_ptr<Shape> shape, int cap, bool own_
   P->shape = shape;
   P->cap = cap;
   P->n = shape->n;
-  P->wn = (size_t)shape->Hx * shape->Py * shape->grid.nz;
+  P->wn = (size_t)shape->Hp * shape->Py * shape->grid.nz;
   P->pstride = std::max((shape->g.nrows + 1) / 2, vec_blocks(shape->n, cap)) + 32;
   const size_t N = P->n * cap;
   Fields& f = P->f;
@@ -768,6 +769,7 @@ std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune;
 int g_radix_order = -1;   // gps_set_radix_order: -1 tunes the radix order, else this one
 int g_x_kernel = -1;      // gps_set_x_kernel: -1 tuned, 0 shared-memory, 1 register-resident (FP32)
+int g_z_kernel = -1;      // gps_set_z_kernel: -1 tuned, 0 plain column kernel, 1 TMA-staged (FP32, df64)
 
 template <typename F>
 float time_launch(F&& launch, cudaStream_t st) {
@@ -850,7 +852,7 @@ void tune_spec(Shape& S, cudaStream_t st) {
       twz = reinterpret_cast<const V*>(S.twz32);
     }
     DevMem tmp;
-    const size_t wn = (size_t)S.Hx * S.Py * S.grid.nz;
+    const size_t wn = (size_t)S.Hp * S.Py * S.grid.nz;
     V* W = tmp.alloc<V>(wn);
     double* in = tmp.alloc<double>(S.n);
     double* outv = tmp.alloc<double>(S.n);
@@ -912,6 +914,7 @@ void tune_spec(Shape& S, cudaStream_t st) {
         if (t < tbest) { tbest = t; best.g.tile_y = tile; best.fy = fy; }
       }
     tbest = 1e30f;
+    best.g.z_tma = 0;
     for (int tile : batch_candidates(S.g.tile_z, S.Pz, sizeof(V), fixz))
       for (int order = 0; order < (fixz ? 1 : norders); ++order) {
         if (!fixz && !order_allowed(S.Pz, order, norders)) continue;
@@ -922,6 +925,13 @@ void tune_spec(Shape& S, cudaStream_t st) {
         const float t = time_launch([&] { launch_z<V>(g, fz, twz, b, a, 1, st); }, st);
         if (t < tbest) { tbest = t; best.g.tile_z = tile; best.fz = fz; }
       }
+    // column kernels: the TMA-staged z pass as one more candidate
+    if (fixz && g_z_kernel != 0) {
+      PassGeom g = best.g;
+      g.z_tma = 1;
+      const float t = time_launch([&] { launch_z<V>(g, best.fz, twz, b, a, 1, st); }, st);
+      if (t < tbest || g_z_kernel == 1) { tbest = t; best.g.z_tma = 1; }
+    }
     ck(cudaStreamSynchronize(st));
     hit = g_tune.emplace(key, best).first;
   }
@@ -1601,6 +1611,7 @@ struct ProfScope {
 int finish(int status, cudaStream_t st) {
   if (cudaStreamSynchronize(st) != cudaSuccess) return GPS_ERR_CUDA;
   if (cudaGetLastError() != cudaSuccess) return GPS_ERR_CUDA;
+  if (take_wait_timeouts()) return GPS_ERR_TIMEOUT;   // a bounded device wait gave up
   return status;
 }
 
@@ -2111,6 +2122,14 @@ int gps_set_x_kernel(int kind) {
   if (kind < -1 || kind > 1) return GPS_ERR_INVALID;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_x_kernel = kind;
+  g_tune.clear();
+  return GPS_OK;
+}
+
+int gps_set_z_kernel(int kind) {
+  if (kind < -1 || kind > 1) return GPS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_z_kernel = kind;
   g_tune.clear();
   return GPS_OK;
 }

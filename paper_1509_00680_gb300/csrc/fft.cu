@@ -11,7 +11,8 @@
 //
 // Each CTA stages a batch of lines in shared memory; the radix stages run
 // out of a shared-memory ping-pong pair with the twiddle table staged once.
-// The spectrum buffer holds only z < nz planes: [nz][Py][Hx] complex.
+// The spectrum buffer holds only z < nz planes: [nz][Py][Hp] complex (Hx
+// values per row, row pitch Hp).
 #include <cstdio>
 #include <type_traits>
 
@@ -285,19 +286,19 @@ __global__ void __launch_bounds__(kThreads) k_y(PassGeom g, FftSched s, const V*
   const int kx0 = blockIdx.x * tile;
   const int nl = min(tile, g.Hx - kx0);   // valid columns of this tile
   const int z = blockIdx.y;
-  const size_t plane = (size_t)z * g.Py * g.Hx;
+  const size_t plane = (size_t)z * g.Py * g.Hp;
   const int nload = DIR < 0 ? g.ny : L;   // forward: rows y >= ny are the zero padding
   // thread -> (column c, first row y0); rows advance by ystep
   const int c = threadIdx.x % tile, y0 = threadIdx.x / tile, ystep = blockDim.x / tile;
   const bool act = c < nl && y0 < ystep;
   V* col = W + plane + kx0 + c;
-  if (act) load_column<V>(b0 + c * ls, col, g.Hx, y0, ystep, L, nload);
+  if (act) load_column<V>(b0 + c * ls, col, g.Hp, y0, ystep, L, nload);
   __syncthreads();
   const V* res = fft_lines<V, DIR, MR>(b0, b1, s, ls, nl, tw, nload);
   const int nstore = DIR < 0 ? L : g.ny;  // inverse: crop to y < ny
   if (act) {
     const V* line = res + c * ls;
-    for (int y = y0; y < nstore; y += ystep) col[(size_t)y * g.Hx] = line[pidx<V>(y)];
+    for (int y = y0; y < nstore; y += ystep) col[(size_t)y * g.Hp] = line[pidx<V>(y)];
   }
 }
 
@@ -321,8 +322,8 @@ __global__ void __launch_bounds__(kThreads) k_z(PassGeom g, FftSched s, const V*
   const int kx0 = blockIdx.x * tile;
   const int nl = min(tile, g.Hx - kx0);
   const int ky = blockIdx.y;
-  const size_t colbase = (size_t)ky * g.Hx + kx0;
-  const size_t zstride = (size_t)g.Py * g.Hx;
+  const size_t colbase = (size_t)ky * g.Hp + kx0;
+  const size_t zstride = (size_t)g.Py * g.Hp;
   // thread -> (column c, first plane z0); planes advance by zstep
   const int c = threadIdx.x % tile, z0 = threadIdx.x / tile, zstep = blockDim.x / tile;
   const bool act = c < nl && z0 < zstep;

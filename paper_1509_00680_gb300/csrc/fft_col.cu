@@ -17,6 +17,7 @@
 #include <cstdio>
 
 #include "fft_common.cuh"
+#include "tma.cuh"
 
 
 
@@ -173,13 +174,13 @@ __global__ void __launch_bounds__(kThreads, (ColCfg<V, L, MODE>::B)) k_col(PassG
   V* col;
   int nload, nstore;
   if constexpr (MODE == COL_Z) {
-    stride = (size_t)g.Py * g.Hx;
-    col = W + (size_t)blockIdx.y * g.Hx + kx;
+    stride = (size_t)g.Py * g.Hp;
+    col = W + (size_t)blockIdx.y * g.Hp + kx;
     nload = g.nz;
     nstore = g.nz;
   } else {
-    stride = g.Hx;
-    col = W + (size_t)blockIdx.y * g.Py * g.Hx + kx;
+    stride = g.Hp;
+    col = W + (size_t)blockIdx.y * g.Py * g.Hp + kx;
     nload = MODE == COL_Y_FWD ? g.ny : L;    // forward: rows y >= ny are the zero padding
     nstore = MODE == COL_Y_FWD ? L : g.ny;   // inverse: crop to y < ny
   }
@@ -256,6 +257,218 @@ void launch_col_len(const PassGeom& g, const V* tw, const Batch& b, const PipeAr
     if (half) launch_col_build<V, L, MODE, true>(g, tw, b, a, nslots, st);
     else launch_col_build<V, L, MODE, false>(g, tw, b, a, nslots, st);
   }
+}
+
+// ---- z pass with TMA-staged column tiles ----------------------------------
+// The same transform, table multiply and inverse as k_col's z mode, but a
+// persistent CTA walks over column tiles (TC adjacent kx of one ky, the nz
+// planes that hold data), and each tile reaches shared memory by tensor
+// loads (boxes of up to 256 planes) issued by one thread, double-buffered:
+// the next tile is in flight while the current one is transformed.  Results
+// go back into the tile and leave by tensor stores.  Per-thread global loads
+// and their address arithmetic disappear from the loop, and the CTA's warps
+// no longer wait on HBM latency between tiles.
+
+constexpr uint32_t kTmaWaitLimit = 1u << 24;   // tests of a barrier before a wait gives up
+__device__ unsigned int g_wait_timeouts;       // waits that gave up since the last check
+
+template <typename V, int L>
+struct ZTile {
+  static constexpr int E = ColCfg<V, L, COL_Z>::E;
+  static constexpr int TPC = L / E, TC = kThreads / TPC, LS = line_stride<V>(L);
+  static constexpr int K8 = (int)(sizeof(V) / 8);   // 8-byte tensor elements per value
+  // resident CTAs per SM asked of the register allocator: 2 (128 registers);
+  // at 3 the df64 tiles spill (the loop keeps more state than k_col)
+  static constexpr int B = 2;
+};
+
+template <typename V, int L, bool HALF>
+__global__ void __launch_bounds__(kThreads, (ZTile<V, L>::B))
+    k_colz_tma(PassGeom g, const V* __restrict__ twg, Batch b, PipeArgs a,
+               const __grid_constant__ CUtensorMap tmap) {
+  using Z = ZTile<V, L>;
+  constexpr int E = Z::E, TPC = Z::TPC, TC = Z::TC, LS = Z::LS, K8 = Z::K8;
+  const int slot = pass_slot<V>(b);
+  if (slot < 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int give_up;
+  const int nz = g.nz;
+  const size_t tile_elems = (size_t)nz * TC;
+  V* tile0 = reinterpret_cast<V*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  V* tile1 = tile0 + tile_elems;
+  V* lines = tile1 + tile_elems;
+  const int c = threadIdx.x % TC, t = threadIdx.x / TC;
+  V* line = lines + c * LS;
+  const V* tw = twg + L;
+  const V* twr = twg + 2 * L;
+  const int nkb = (g.Hx + TC - 1) / TC;
+  const int ntiles = nkb * g.Py;
+  const uint32_t tile_bytes = (uint32_t)(tile_elems * sizeof(V));
+  const int nbox = (nz + 255) / 256;
+  auto issue = [&](int tile, V* dst, uint64_t* br) {
+    const int kb = tile % nkb, ky = tile / nkb;
+    mbar_arrive_expect_tx(br, tile_bytes);
+    for (int bx = 0; bx < nbox; ++bx)
+      tma_load_4d(dst + (size_t)bx * 256 * TC, &tmap, kb * TC * K8, ky, bx * 256, slot, br);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+    give_up = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, tile0, &bar[0]);
+  const int hy = g.Py / 2 + 1;
+  const size_t tz = (size_t)hy * g.Hx;
+  const bool use_k0 = a.slot_k0 && b.st && b.st[slot].use_k0;
+  constexpr int R0 = ColPlan<L>::radix(0, false);
+  constexpr int RL = ColPlan<L>::radix(ColPlan<L>::nst - 1, false);
+  int i = 0;
+  bool pending_next = false;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+    V* cur = (i & 1) ? tile1 : tile0;
+    V* nxt = (i & 1) ? tile0 : tile1;
+    const int next = tile + gridDim.x;
+    if (threadIdx.x == 0) {
+      pending_next = false;
+      if (next < ntiles) {
+        bulk_wait_read_all();             // the store of the previous tile has read nxt
+        issue(next, nxt, &bar[(i + 1) & 1]);
+        pending_next = true;
+      }
+    }
+    if (!mbar_wait_bounded(&bar[i & 1], (uint32_t)(i >> 1) & 1u, kTmaWaitLimit)) give_up = 1;
+    __syncthreads();
+    if (give_up) break;
+    const int kb = tile % nkb, ky = tile / nkb;
+    const int kx = kb * TC + c;
+    const bool act = kx < g.Hx;
+    V x[E];
+#pragma unroll
+    for (int q = 0; q < E / R0; ++q)
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        const int row = t + q * TPC + r * (L / R0);
+        if (HALF && r >= R0 / 2) x[q * R0 + r] = czero<V>();
+        else x[q * R0 + r] = row < nz ? cur[(size_t)row * TC + c] : czero<V>();
+      }
+    col_stages<V, L, E, -1, false, 0, HALF>(x, t, tw, line);
+    const int kyp = min(ky, g.Py - ky);
+    const size_t t0 = (size_t)kyp * g.Hx + (act ? kx : 0);
+    const bool at0 = use_k0 && kx == 0 && ky == 0;
+#pragma unroll
+    for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int kz = t + q * TPC + r * (L / RL);
+        const int kzp = min(kz, L - kz);
+        typename Real<V>::T tv = table_value<V>(a, t0 + (size_t)kzp * tz);
+        if (at0 && kz == 0) tv = real_of<V>(b.st[slot].k0);
+        x[q * RL + r] = cscale(x[q * RL + r], tv);
+      }
+    col_stages<V, L, E, +1, true, 0>(x, t, twr, line);
+#pragma unroll
+    for (int q = 0; q < E / R0; ++q)
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        const int row = t + q * TPC + r * (L / R0);
+        if (row < nz) cur[(size_t)row * TC + c] = x[q * R0 + r];
+      }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int bx = 0; bx < nbox; ++bx)
+        tma_store_4d(&tmap, kb * TC * K8, ky, bx * 256, slot, cur + (size_t)bx * 256 * TC);
+      bulk_commit();
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (give_up) {
+      // this tile's load and the prefetch of the next may still be in
+      // flight: wait for them (bounded) before the CTA's shared memory goes
+      mbar_wait_bounded(&bar[i & 1], (uint32_t)(i >> 1) & 1u, kTmaWaitLimit);
+      if (pending_next) mbar_wait_bounded(&bar[(i + 1) & 1], (uint32_t)((i + 1) >> 1) & 1u, kTmaWaitLimit);
+      atomicAdd(&g_wait_timeouts, 1u);
+      if (b.st) {
+        b.st[slot].status = GPS_ERR_TIMEOUT;
+        b.st[slot].phase = PH_DONE;
+      }
+    }
+    bulk_wait_all();                      // stores done before shared memory is released
+  }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library); null if unavailable.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of the spectrum seen by the z pass: dims (8-byte elements of a
+// row, ky, z, slot), strides from the row pitch Hp and the slot stride; box
+// TC values x 1 x min(nz, 256) x 1.
+template <typename V, int L>
+bool encode_z_map(CUtensorMap* map, void* W, const PassGeom& g, size_t wstride, int nslots) {
+  using Z = ZTile<V, L>;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || !W || (reinterpret_cast<uintptr_t>(W) & 15)) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.Hx * Z::K8, (cuuint64_t)g.Py, (cuuint64_t)g.nz,
+                              (cuuint64_t)(nslots > 0 ? nslots : 1)};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.Hp * sizeof(V), (cuuint64_t)g.Py * g.Hp * sizeof(V),
+                                 (cuuint64_t)(wstride ? wstride : (size_t)g.Py * g.Hp * g.nz) * sizeof(V)};
+  for (cuuint64_t s : strides)
+    if (s % 16) return false;
+  const cuuint32_t box[4] = {(cuuint32_t)(Z::TC * Z::K8), 1u, (cuuint32_t)(g.nz < 256 ? g.nz : 256), 1u};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, W, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename V, int L, bool HALF>
+bool launch_colz_tma_build(const PassGeom& g, const V* tw, const Batch& b, const PipeArgs& a, int nslots,
+                           cudaStream_t st) {
+  using Z = ZTile<V, L>;
+  // boxes of 256 planes must tile nz exactly (the tile in shared memory holds nz planes)
+  if (g.nz % 2 || g.nz > 1024 || (g.nz > 256 && g.nz % 256)) return false;
+  CUtensorMap map;
+  if (!encode_z_map<V, L>(&map, a.W, g, a.wstride, nslots)) return false;
+  const size_t sm = 128 + 2 * (size_t)g.nz * Z::TC * sizeof(V) + (size_t)Z::TC * Z::LS * sizeof(V);
+  if (sm + kStaticSmemAllowance > 227 * 1024) return false;
+  if (cudaFuncSetAttribute(k_colz_tma<V, L, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+      cudaSuccess)
+    return false;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_colz_tma<V, L, HALF>, kThreads, sm) !=
+          cudaSuccess ||
+      per_sm < 1)
+    return false;
+  const int ntiles = ((g.Hx + Z::TC - 1) / Z::TC) * g.Py;
+  const int ns = nslots > 0 ? nslots : 1;
+  int nb = (152 * per_sm + ns - 1) / ns;
+  if (nb > ntiles) nb = ntiles;
+  if (nb < 1) nb = 1;
+  count_launch();
+  k_colz_tma<V, L, HALF><<<dim3(nb, 1, ns), kThreads, sm, st>>>(g, tw, b, a, map);
+  return true;
+}
+
+template <typename V, int L>
+bool launch_colz_tma_len(const PassGeom& g, const V* tw, const Batch& b, const PipeArgs& a, int nslots,
+                         cudaStream_t st) {
+  if (2 * g.nz == L) return launch_colz_tma_build<V, L, true>(g, tw, b, a, nslots, st);
+  return launch_colz_tma_build<V, L, false>(g, tw, b, a, nslots, st);
 }
 
 template <typename V, int MODE>
@@ -460,6 +673,13 @@ template bool launch_xr_pass<float2>(bool, int, const PassGeom&, const float2*, 
 template bool launch_xr_pass<dfc>(bool, int, const PassGeom&, const dfc*, const Batch&,
                                   const PipeArgs&, int, cudaStream_t);
 
+unsigned int take_wait_timeouts() {
+  unsigned int n = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&n, g_wait_timeouts, sizeof(n)) != cudaSuccess) return 0;
+  if (n) cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(zero));
+  return n;
+}
+
 bool col_pass_supported(int L) {
   return L == 64 || L == 128 || L == 256 || L == 512 || L == 1024;
 }
@@ -500,7 +720,22 @@ bool launch_col_pass(int mode, int L, const PassGeom& g, const V* tw, const Batc
   switch (mode) {
     case COL_Y_FWD: return launch_col_mode<V, COL_Y_FWD>(L, g, tw, b, a, nslots, st);
     case COL_Y_INV: return launch_col_mode<V, COL_Y_INV>(L, g, tw, b, a, nslots, st);
-    default: return launch_col_mode<V, COL_Z>(L, g, tw, b, a, nslots, st);
+    default:
+      // z pass: the TMA-staged kernel where the tuner chose it (and a tensor
+      // map could be made), else the plain register-resident one
+      if (g.z_tma) {
+        bool done = false;
+        switch (L) {
+          case 64: done = launch_colz_tma_len<V, 64>(g, tw, b, a, nslots, st); break;
+          case 128: done = launch_colz_tma_len<V, 128>(g, tw, b, a, nslots, st); break;
+          case 256: done = launch_colz_tma_len<V, 256>(g, tw, b, a, nslots, st); break;
+          case 512: done = launch_colz_tma_len<V, 512>(g, tw, b, a, nslots, st); break;
+          case 1024: done = launch_colz_tma_len<V, 1024>(g, tw, b, a, nslots, st); break;
+          default: break;
+        }
+        if (done) return true;
+      }
+      return launch_col_mode<V, COL_Z>(L, g, tw, b, a, nslots, st);
   }
 }
 

@@ -216,7 +216,7 @@ __host__ __device__ constexpr int line_stride(int L) { return L + (L >> PadShift
 
 __device__ __forceinline__ size_t row_offset(const PassGeom& g, int row) {
   const int y = row % g.ny, z = row / g.ny;
-  return ((size_t)z * g.Py + y) * g.Hx;
+  return ((size_t)z * g.Py + y) * g.Hp;
 }
 
 constexpr int kThreads = 256;

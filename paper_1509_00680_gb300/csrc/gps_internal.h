@@ -98,14 +98,20 @@ struct SlotState {
 };
 
 // Geometry of the FFT passes, shared by every slot of a pool.
+// Row pitch of a spectrum row of Hx complex values.
+inline int spectrum_pitch(int Hx) { return Hx + (Hx & 1); }
+
 struct PassGeom {
   int nx, ny, nz;      // real grid
   int Px, Py, Pz;      // padded transform lengths
   int Hx;              // Px/2 + 1
+  int Hp;              // row pitch of the spectrum (elements): Hx rounded up to even, so
+                       // that every spectrum row starts on a 16-byte boundary
   int nrows;           // ny*nz (rows of the x passes)
   int lines_x;         // row pairs per CTA in the x passes
   int tile_y, tile_z;  // columns per CTA in the y / z passes
   int x_reg;           // FP32 spectrum: 1 = x passes by the register-resident kernels
+  int z_tma;           // FP32 / df64 spectrum: 1 = z pass by the TMA-staged kernel
 };
 
 // Slot addressing of one launch.  active == nullptr: slot 0 only, no phase
@@ -175,6 +181,9 @@ void launch_x_inv(const PassGeom& g, const FftSched& s, const V* tw, const Batch
 // 3 L entries: the plain table and the two per-stage layouts whose plain
 // indices col_stage_twiddle_index(L, idx[2 L]) writes (forward, reversed).
 bool col_pass_supported(int L);
+// Bounded device waits (TMA-staged passes) that gave up since the last call;
+// resets the count.
+unsigned int take_wait_timeouts();
 bool col_stage_twiddle_index(int L, int* idx);
 // Register-resident x passes (same lengths and twiddle requirement; used
 // for the df64 spectrum).

@@ -96,7 +96,8 @@ extern "C" int gps_vacuum_solve_noalloc(const gps_grid* grid, const double* sigm
   const size_t off_twz = off_twy + align256((size_t)Py * sizeof(double2));
   const size_t off_tab = off_twz + align256((size_t)Pz * sizeof(double2));
   const size_t off_w = off_tab + align256(table_n * sizeof(double));
-  const size_t need = off_w + (size_t)Hx * Py * grid->nz * sizeof(double2);
+  const int Hp = spectrum_pitch(Hx);
+  const size_t need = off_w + (size_t)Hp * Py * grid->nz * sizeof(double2);
   if (need > kScratchBytes) return GPS_ERR_INVALID;   // beyond the fixed scratch size
 
   int device = 0;
@@ -131,7 +132,7 @@ extern "C" int gps_vacuum_solve_noalloc(const gps_grid* grid, const double* sigm
 
   PassGeom g;
   g.nx = grid->nx; g.ny = grid->ny; g.nz = grid->nz;
-  g.Px = Px; g.Py = Py; g.Pz = Pz; g.Hx = Hx;
+  g.Px = Px; g.Py = Py; g.Pz = Pz; g.Hx = Hx; g.Hp = Hp;
   g.nrows = grid->ny * grid->nz;
   g.lines_x = default_lines(Px, (g.nrows + 1) / 2, sizeof(double2));
   g.tile_y = default_lines(Py, Hx * grid->nz, sizeof(double2));

@@ -92,6 +92,7 @@ _SIGS = {
     "gps_vacuum_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(gps_grid), _P, _P, _P]),
     "gps_set_radix_order": (ctypes.c_int, [ctypes.c_int]),
     "gps_set_x_kernel": (ctypes.c_int, [ctypes.c_int]),
+    "gps_set_z_kernel": (ctypes.c_int, [ctypes.c_int]),
     "gps_sccs_eps": (ctypes.c_int, [_P, ctypes.c_size_t, _P, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, _P, _P, _P]),
     "gps_polarization_charge": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P, _P, _P]),
@@ -336,6 +337,11 @@ def set_radix_order(order):
 def set_x_kernel(kind):
     """FP32 x passes: -1 tuned (default), 0 shared-memory kernels, 1 register-resident."""
     _check(load().gps_set_x_kernel(int(kind)), "gps_set_x_kernel")
+
+
+def set_z_kernel(kind):
+    """FP32 / df64 z pass: -1 tuned (default), 0 plain column kernel, 1 TMA-staged."""
+    _check(load().gps_set_z_kernel(int(kind)), "gps_set_z_kernel")
 
 
 def make_request(grid, kind, rho, eps, phi, electrolyte=None, opts=None):

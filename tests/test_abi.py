@@ -92,6 +92,8 @@ def test_new_defaults_and_host_side_argument_checks(lib):
     assert L.gps_set_x_kernel(2) == gps.GPS_ERR_INVALID
     assert L.gps_set_x_kernel(-2) == gps.GPS_ERR_INVALID
     assert L.gps_set_x_kernel(-1) == gps.GPS_OK
+    assert L.gps_set_z_kernel(2) == gps.GPS_ERR_INVALID
+    assert L.gps_set_z_kernel(-1) == gps.GPS_OK
     g = gps.gps_grid()
     rep = gps.gps_report()
     assert L.gps_gpe_solve(None, ctypes.byref(g), None, None, None, ctypes.byref(o), ctypes.byref(rep),

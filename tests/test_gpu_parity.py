@@ -230,6 +230,50 @@ def test_precondition_fp32_x_kernels(gps, bc, n, h, kind):
         gps.set_x_kernel(-1)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("df64", 1e-12)])
+@pytest.mark.parametrize("bc,n,h", COLUMN[:6])
+def test_precondition_tma_z_pass(gps, bc, n, h, prec, tol):
+    """The z pass of the FP32 and double-float spectra in its TMA-staged form
+    (tensor loads and stores of column tiles, persistent CTAs), forced: the
+    preconditioner against the oracle at each spectrum's tolerance, for the
+    column lengths 128-1024, zero-padded and periodic."""
+    g = _grid(bc, n, h)
+    rng = np.random.default_rng(24)
+    eps = 1.0 + 30.0 * rng.random(g.shape)
+    r = rng.standard_normal(g.shape)
+    f = Fields(g, eps)
+    gps.set_z_kernel(1)
+    c = gps.Context(0)
+    try:
+        v = T(np.zeros(g.shape))
+        code = gps.GPS_MIXED if prec == "fp32" else gps.GPS_DF64
+        c.precondition(gps.grid_from(g), T(f.s), T(r), v, precision=code)
+        assert relmax(N(v, g.shape), f.precondition(r)) < tol
+    finally:
+        c.close()
+        gps.set_z_kernel(-1)
+
+
+def test_mixed_solve_tma_z_pass(gps):
+    """A mixed-precision solve (df64 then FP32 spectrum) with the TMA-staged
+    z pass forced, against the oracle at the mixed bar."""
+    p = synth.workload(4, n=64, count=12, margin=6.0, kind="gpe")
+    gps.set_z_kernel(1)
+    c = gps.Context(0)
+    try:
+        phi = T(np.zeros(p.grid.shape))
+        rep = c.gpe_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), phi,
+                          gps.default_opts(tol_abs=1e-10, precision=gps.GPS_MIXED_DF64, max_iter=2000))
+        ref, _ = oracle.solve_gpe(p.grid, p.rho, p.eps, tol_abs=0.0, tol_rel=1e-13, max_iter=2000)
+        assert rep.status == 0 and 0 < rep.fp64_iters < rep.iters
+        assert 0 <= rep.fixed_point_res < 1e-8
+        err = rel2(N(phi, p.grid.shape), ref)
+        assert err <= 1e-8, err
+    finally:
+        c.close()
+        gps.set_z_kernel(-1)
+
+
 def _has_solvent(p):
     """A slab test box must reach above the interface (z = 10 bohr): below it
     eps = 1 and the problem is vacuum Poisson."""
