@@ -677,8 +677,9 @@ def run_serving(gps, device, args):
                     latency of a sustainable load;
       fp64 / mixed  the plain FP64 path (FP64 spectrum, one solve per call
       sequential    through the host-array entry points, as a served request
-                    arrives) and the mixed path the same way, on every k-th
-                    request (a uniform sample of `--serving-fp64-sample`)."""
+                    arrives) on every request of the stream, and the mixed
+                    path the same way on a uniform sample
+                    (`--serving-mixed-sample` requests)."""
     import threading
     import synth
     count = args.serving_count
@@ -700,21 +701,40 @@ def run_serving(gps, device, args):
         r = gps.make_request(gps.grid_from(p.grid), kind, rho, eps, phi, el, opts)
         return r, (rho, eps, phi)
 
+    secs = {}
+
+    def note(name, value):
+        secs[name] = value
+        print("serving: %s %.2f s" % (name, value), file=sys.stderr, flush=True)
+
+    tw0 = time.perf_counter()
     made = [make(i, mixed_opts()) for i in range(count)]
+    note("inputs", time.perf_counter() - tw0)
     first = {}
     for i, (edge, bc, kind, _) in enumerate(desc):
         first.setdefault((edge, bc, kind), i)
     budget = 120 << 30
     ctx = gps.Context(device, budget)
+    tw0 = time.perf_counter()
     gps.batch_solve(ctx, [made[i][0] for i in first.values()], allow=(0, 3))    # plans, graphs
+    note("warmup", time.perf_counter() - tw0)
     ncap = min(count, args.serving_capacity_count)
     t0 = time.perf_counter()
     reps_b = gps.batch_solve(ctx, [m[0] for m in made[:ncap]], allow=(0, 3))
-    capacity = ncap / (time.perf_counter() - t0)
+    note("capacity", time.perf_counter() - t0)
+    capacity = ncap / secs["capacity"]
     ctx.close()
 
+    # one server for both streams, warmed (untimed) with one request per
+    # distinct grid and problem: tables, plans and graphs are in place, as in
+    # a server that has been running
+    srv = gps.Server(device, hbm_budget_bytes=budget)
+    tw0 = time.perf_counter()
+    for st_, _ in [srv.wait(t, timeout=1800) for t in [srv.submit(made[i][0], keep=made[i][1]) for i in first.values()]]:
+        pass
+    note("server_warmup", time.perf_counter() - tw0)
+
     def stream(n, rate, seed):
-        srv = gps.Server(device, hbm_budget_bytes=budget)
         rng = np.random.default_rng(seed)
         tickets, keep = [], []
         start = time.perf_counter()
@@ -729,26 +749,29 @@ def run_serving(gps, device, args):
         th = threading.Thread(target=producer)
         th.start()
         th.join()
-        results = [srv.wait(t) for t in tickets]
+        results = [srv.wait(t, timeout=1800) for t in tickets]
         wall = time.perf_counter() - start
-        stats = srv.stats()
-        srv.close()
-        return results, wall, stats
+        return results, wall, srv.stats()
 
     rate = 1.5 * capacity
     results, wall, stats = stream(count, rate, 77)
+    note("saturated", wall)
     lat = sorted(rep.time_ms for _, rep in results)
     ok = sum(1 for st_, _ in results if st_ == 0)
     nlow = min(count, args.serving_low_count)
     res_l, wall_l, _ = stream(nlow, 0.5 * capacity, 78)
+    note("low_load", wall_l)
+    srv.close()
     lat_l = sorted(rep.time_ms for _, rep in res_l)
 
-    # sequential single solves on a uniform sample: plain FP64, then mixed
-    k = max(1, count // max(1, args.serving_fp64_sample))
-    sample = list(range(0, count, k))
+    # sequential single solves: plain FP64 on every request of the stream,
+    # mixed on a uniform sample
+    k = max(1, count // max(1, args.serving_mixed_sample))
+    samples = {"fp64": list(range(count)), "mixed_df64": list(range(0, count, k))}
     seq = {}
     ctx = gps.Context(device, budget)
     for name, prec in (("fp64", gps.GPS_FP64), ("mixed_df64", gps.GPS_MIXED_DF64)):
+        sample = samples[name]
         for i in sorted({(desc[j][0], desc[j][1], desc[j][2]): j for j in sample}.values()):
             run_single(gps, ctx, reqs[i], prec)                      # plans and tuning, untimed
         t0 = time.perf_counter()
@@ -756,6 +779,7 @@ def run_serving(gps, device, args):
         for i in sample:
             st_ok += run_single(gps, ctx, reqs[i], prec) == 0
         dt = time.perf_counter() - t0
+        note("sequential_" + name, dt)
         seq[name] = {"solves_per_s": len(sample) / dt, "ok": st_ok}
     ctx.close()
     served = count / wall
@@ -769,8 +793,9 @@ def run_serving(gps, device, args):
                                  "p50_ms": float(np.percentile(lat_l, 50)),
                                  "p99_ms": float(np.percentile(lat_l, 99)),
                                  "ok": sum(1 for st_, _ in res_l if st_ == 0)},
-            "sequential": {"sample": "every %d-th request (%d of %d), one solve per call through the "
-                                     "host-array entry points" % (k, len(sample), count),
+            "sequential": {"how": "one solve per call through the host-array entry points; FP64 on all %d "
+                                  "requests of the stream, mixed df64 on every %d-th (%d)"
+                                  % (count, k, len(samples["mixed_df64"])),
                            "fp64_solves_per_s": seq["fp64"]["solves_per_s"],
                            "mixed_df64_solves_per_s": seq["mixed_df64"]["solves_per_s"],
                            "ok": {n: v["ok"] for n, v in seq.items()}},
@@ -778,7 +803,8 @@ def run_serving(gps, device, args):
             "max_concurrent": stats["max_concurrent"],
             "pool_bytes": stats["bytes_in_use"],
             "precision": "mixed_df64 (FP32 spectrum after the switch, df64 before, FP64 certificate)",
-            "max_certificate": float(max(rep.fixed_point_res for _, rep in results))}
+            "max_certificate": float(max(rep.fixed_point_res for _, rep in results)),
+            "seconds": {k: round(v, 2) for k, v in secs.items()}}
 
 
 def run_single(gps, ctx, req, precision):
@@ -1105,7 +1131,7 @@ def main():
     ap.add_argument("--serving-count", type=int, default=512)
     ap.add_argument("--serving-capacity-count", type=int, default=128)
     ap.add_argument("--serving-low-count", type=int, default=48)
-    ap.add_argument("--serving-fp64-sample", type=int, default=32)
+    ap.add_argument("--serving-mixed-sample", type=int, default=64)
     ap.add_argument("--passes", default=None, choices=sorted(PASS_CASES),
                     help="per-pass times of one preconditioner application instead of the bench")
     ap.add_argument("--precisions", default="fp64,df64,fp32")

@@ -66,6 +66,7 @@ typedef enum {
 typedef enum { GPS_FP64 = 0, GPS_MIXED = 1, GPS_DF64 = 2, GPS_MIXED_DF64 = 3 } gps_precision;
 typedef enum { GPS_GPE = 0, GPS_LPB = 1, GPS_NLPB = 2, GPS_MPB = 3 } gps_problem;
 typedef enum { GPS_OUTER_NEWTON = 0, GPS_OUTER_PRINTED = 1 } gps_outer_mode;
+typedef enum { GPS_FORCING_EW2 = 0, GPS_FORCING_RATIO = 1 } gps_forcing_rule;
 
 /* Solver of the generalized Poisson equation (gps_opts.method; accepted by
  * gps_gpe_solve and gps_gpe_solve_host only, with precision GPS_FP64 and
@@ -144,8 +145,8 @@ typedef struct {
   double tol_outer;      /* NLPB outer tolerance on the ionic-charge residual */
   double eta;            /* mixing: NLPB printed Algorithm 4; GPS_SC rho_iter (Algorithm 1) */
   int outer_mode;        /* gps_outer_mode */
-  double forcing;        /* NLPB Newton: cap of the inner solve's relative tolerance, which is
-                            min(forcing, F/F_0) (F the outer residual); in (0, 1) */
+  double forcing;        /* NLPB Newton: cap of the inner solve's relative tolerance eta_k
+                            (see forcing_rule); in (0, 1) */
   int precision;         /* gps_precision */
   double mixed_switch;   /* GPS_MIXED(_DF64): high-precision preconditioner until
                             ||r|| <= mixed_switch*||r_0|| (nonlinear PB: r_0 of the first outer step) */
@@ -162,6 +163,14 @@ typedef struct {
   int method;            /* gps_method (GPS_PCG) */
   double alpha;          /* GPS_PSD: fixed step length; 0 = steepest-descent step */
   int diis;              /* GPS_PSD: DIIS history length 0..GPS_MAX_DIIS (0 and 1: plain PSD) */
+  int forcing_rule;      /* NLPB Newton, inner tolerance eta_k relative to the inner solve's
+                            initial residual (F_k the outer residual of step k):
+                            GPS_FORCING_EW2 (default) Eisenstat & Walker's choice 2: eta_0 =
+                            forcing, eta_k = 0.9 (F_k/F_(k-1))^2, raised to 0.9 eta_(k-1)^2 when
+                            that exceeds 0.1, capped at forcing;
+                            GPS_FORCING_RATIO: eta_k = min(forcing, F_k/F_0).
+                            Both reach the same solution; they differ in how far each inner
+                            solve is taken. */
 } gps_opts;
 
 typedef struct {
@@ -427,6 +436,15 @@ int gps_set_x_kernel(int kind);
  * of the TMA-staged kernel that gives up makes the call return
  * GPS_ERR_TIMEOUT.  Clears the process-wide tuning cache. */
 int gps_set_z_kernel(int kind);
+
+/* Scheduling of the batching engine (gps_batch_solve and servers created
+ * afterwards), for measurements: 1 (the default) every pool of the engine
+ * advances on its own -- a pool whose round of PCG iterations has finished
+ * is collected, takes queued requests into its free slots and starts its
+ * next round while the other pools' rounds run, with more iterations per
+ * round for small pools; 0 lockstep -- one round of four iterations on
+ * every busy pool, then all pools are synchronized and collected. */
+int gps_set_engine_mode(int async);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 unsigned long long gps_kernel_launches(void);

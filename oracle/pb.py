@@ -111,7 +111,7 @@ def alg3(grid, rho, eps, electrolyte, eps0, eta=0.6, tol=1e-10, max_outer=200,
 
 def alg4(grid, rho, eps, electrolyte, eps0, mode="newton", eta=0.6, tol=1e-10,
          max_outer=100, gamma=None, max_iter=2000, loose_rel=1e-4, loose_steps=2,
-         forcing=1e-2, record=False):
+         forcing=1e-2, forcing_rule="ratio", record=False):
     """Algorithm 4 with an optionally linearized inner operator.
 
     State after each outer step: phi, the effective ionic charge rho_ions and
@@ -128,8 +128,15 @@ def alg4(grid, rho, eps, electrolyte, eps0, mode="newton", eta=0.6, tol=1e-10,
       inner solves loose, then the outer criterion in residual units).
     mode "newton": eta = 1, lambda = -4 pi d rho_ions/d phi at phi (the
       linear PB term of Eq. corrPB at the current potential) and t halved
-      until the nonlinear residual decreases; inner tolerance
-      min(forcing, ||F_k||/||F_0||) relative, floored at the outer one.
+      until the nonlinear residual decreases; inner tolerance relative to the
+      inner solve's initial residual, floored at the outer one:
+        forcing_rule "ratio": eta_k = min(forcing, ||F_k|| / ||F_0||);
+        forcing_rule "ew2":   Eisenstat & Walker's choice 2 (SIAM J. Sci.
+          Comput. 17 (1996)), eta_0 = forcing, eta_k = 0.9 (||F_k|| /
+          ||F_(k-1)||)^2, raised to 0.9 eta_(k-1)^2 when that exceeds 0.1,
+          capped at forcing.
+      Both leave the fixed point unchanged; they differ in how far each
+      inner solve is taken.
     Outer residual: ||rho_ions[phi] - rho_ions + r'||_2 (the charge-unit
     residual of A phi + 4 pi (rho + rho_ions[phi]) = 0)."""
     gamma = exclusion_from_eps(eps, eps0) if gamma is None else gamma
@@ -140,6 +147,7 @@ def alg4(grid, rho, eps, electrolyte, eps0, mode="newton", eta=0.6, tol=1e-10,
     hist, inner, steps = [], [], []
     vac = None
     F0 = None
+    F_prev = eta_prev = None
     for k in range(max_outer):
         fresh = ionic_charge(phi, gamma, electrolyte)
         F = float(np.sqrt(np.sum((fresh - rions + rp) ** 2)))
@@ -161,7 +169,17 @@ def alg4(grid, rho, eps, electrolyte, eps0, mode="newton", eta=0.6, tol=1e-10,
             else:
                 kw = dict(tol_abs=4.0 * np.pi * tol)
         else:
-            kw = dict(tol_abs=4.0 * np.pi * tol * 0.1, tol_rel=min(forcing, F / F0))
+            if forcing_rule == "ew2" and F_prev is not None:
+                eta_k = 0.9 * (F / F_prev) ** 2
+                if 0.9 * eta_prev ** 2 > 0.1:
+                    eta_k = max(eta_k, 0.9 * eta_prev ** 2)
+                eta_k = min(eta_k, forcing)
+            elif forcing_rule == "ew2":
+                eta_k = forcing
+            else:
+                eta_k = min(forcing, F / F0)
+            F_prev, eta_prev = F, eta_k
+            kw = dict(tol_abs=4.0 * np.pi * tol * 0.1, tol_rel=eta_k)
         dphi, info = pcg(fields, src, max_iter=max_iter, **kw)
         inner.append(info["iters"])
         rpp = -info["r"] / (4.0 * np.pi)

@@ -76,6 +76,7 @@ struct SlotState {
   double aux[8];        // results of one-off reductions
   // nonlinear PB (Algorithm 4)
   double F, F0, t, tol_outer, eta, forcing, lam_sum, eps_sum;
+  double F_prev, eta_prev;  // Newton: previous outer residual and inner tolerance (forcing rule)
   double cert;          // ||g|| / ||phi||, -1 if not computed
   double rr_min;        // smallest ||r||^2 seen in the FP32 phase
   double rr_switch;     // ||r||^2 below which the FP32 spectrum takes over (mixed)
@@ -88,6 +89,7 @@ struct SlotState {
   int mixed, spec, spec_hi, restart, certify;   // spec: spectrum precision in use
   int mixed_req;        // the caller asked for a mixed precision (nonlinear PB: each inner solve)
   int newton, outer, max_outer, bad_eps;
+  int forcing_ew;       // Newton inner tolerance by Eisenstat-Walker choice 2 (else min(forcing, F/F0))
   // Set by the x inverse pass once v and (v, r) of this iteration exist,
   // and by update_p once p, A p and alpha do; each update kernel acts only
   // on its predecessor's flag (a pipeline of another precision may have

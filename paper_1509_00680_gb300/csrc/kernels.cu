@@ -238,6 +238,8 @@ __global__ void k_setup_phase(Batch b, size_t n, double inv_p, int periodic) {
   S.fp64_iters = 0;
   S.outer = 0;
   S.F0 = -1.0;
+  S.F_prev = -1.0;
+  S.eta_prev = 0.0;
   S.F = 0.0;
   S.cert = -1.0;
   S.phase = S.kind == GPS_NLPB ? PH_NLEVAL : PH_INIT;
@@ -514,7 +516,21 @@ __global__ void k_nl_eval(Batch b, Fields f, size_t n, double inv_p, int periodi
     } else {
       if (S.newton) {
         S.tol_abs = 0.1 * kFourPi * S.tol_outer;
-        S.tol_rel = fmin(S.forcing, F / S.F0);
+        double eta = fmin(S.forcing, F / S.F0);
+        if (S.forcing_ew) {
+          // Eisenstat-Walker choice 2 (gamma 0.9, exponent 2) with its safeguard
+          eta = S.forcing;
+          if (S.F_prev > 0.0) {
+            const double q = F / S.F_prev;
+            eta = 0.9 * q * q;
+            const double sg = 0.9 * S.eta_prev * S.eta_prev;
+            if (sg > 0.1) eta = fmax(eta, sg);
+            eta = fmin(eta, S.forcing);
+          }
+        }
+        S.tol_rel = eta;
+        S.F_prev = F;
+        S.eta_prev = eta;
       } else if (S.outer < 2) {
         S.tol_abs = 0.0;
         S.tol_rel = 1e-4;

@@ -19,6 +19,7 @@ GPS_BC_FREE, GPS_BC_PERIODIC, GPS_BC_SURFACE, GPS_BC_WIRE = 0, 1, 2, 3
 GPS_FP64, GPS_MIXED, GPS_DF64, GPS_MIXED_DF64 = 0, 1, 2, 3
 GPS_GPE, GPS_LPB, GPS_NLPB, GPS_MPB = 0, 1, 2, 3
 GPS_OUTER_NEWTON, GPS_OUTER_PRINTED = 0, 1
+GPS_FORCING_EW2, GPS_FORCING_RATIO = 0, 1
 GPS_PCG, GPS_SC, GPS_PSD = 0, 1, 2
 GPS_MAX_DIIS = 8
 METHOD = {"pcg": GPS_PCG, "sc": GPS_SC, "psd": GPS_PSD}
@@ -47,7 +48,8 @@ class gps_opts(ctypes.Structure):
                 ("outer_mode", ctypes.c_int), ("forcing", ctypes.c_double),
                 ("precision", ctypes.c_int), ("mixed_switch", ctypes.c_double),
                 ("certify", ctypes.c_int), ("warm_start", ctypes.c_int),
-                ("method", ctypes.c_int), ("alpha", ctypes.c_double), ("diis", ctypes.c_int)]
+                ("method", ctypes.c_int), ("alpha", ctypes.c_double), ("diis", ctypes.c_int),
+                ("forcing_rule", ctypes.c_int)]
 
 
 class gps_report(ctypes.Structure):
@@ -93,6 +95,7 @@ _SIGS = {
     "gps_set_radix_order": (ctypes.c_int, [ctypes.c_int]),
     "gps_set_x_kernel": (ctypes.c_int, [ctypes.c_int]),
     "gps_set_z_kernel": (ctypes.c_int, [ctypes.c_int]),
+    "gps_set_engine_mode": (ctypes.c_int, [ctypes.c_int]),
     "gps_sccs_eps": (ctypes.c_int, [_P, ctypes.c_size_t, _P, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, _P, _P, _P]),
     "gps_polarization_charge": (ctypes.c_int, [_P, ctypes.POINTER(gps_grid), _P, _P, _P, _P, _P]),
@@ -344,6 +347,11 @@ def set_z_kernel(kind):
     _check(load().gps_set_z_kernel(int(kind)), "gps_set_z_kernel")
 
 
+def set_engine_mode(asynchronous):
+    """Batching engine: True pools advance independently (default), False lockstep."""
+    _check(load().gps_set_engine_mode(1 if asynchronous else 0), "gps_set_engine_mode")
+
+
 def make_request(grid, kind, rho, eps, phi, electrolyte=None, opts=None):
     """A gps_request over host arrays (C-contiguous float64 numpy arrays that
     must stay alive until the request completes)."""
@@ -394,9 +402,22 @@ class Server:
         self._keep.pop(ticket, None)
         return s, rep
 
-    def wait(self, ticket):
+    def wait(self, ticket, timeout=None):
+        """(status, report) of a ticket once it is done.  timeout (seconds):
+        poll instead of blocking, and raise TimeoutError past the deadline."""
         rep = gps_report()
-        s = load().gps_server_wait(self.handle, ctypes.c_ulonglong(ticket), ctypes.byref(rep))
+        if timeout is None:
+            s = load().gps_server_wait(self.handle, ctypes.c_ulonglong(ticket), ctypes.byref(rep))
+        else:
+            import time
+            deadline = time.monotonic() + timeout
+            while True:
+                s = load().gps_server_poll(self.handle, ctypes.c_ulonglong(ticket), ctypes.byref(rep))
+                if s != GPS_PENDING:
+                    break
+                if time.monotonic() > deadline:
+                    raise TimeoutError("server ticket %d not done after %.0f s" % (ticket, timeout))
+                time.sleep(0.002)
         self._keep.pop(ticket, None)
         return s, rep
 

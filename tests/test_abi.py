@@ -84,6 +84,7 @@ def test_new_defaults_and_host_side_argument_checks(lib):
     from paper_1509_00680_gb300 import gps
     o = gps.default_opts()
     assert o.forcing == 0.3 and o.eta == 0.6 and o.method == gps.GPS_PCG
+    assert o.forcing_rule == 0            # GPS_FORCING_EW2
     assert o.alpha == 0.0 and o.diis == 0 and o.warm_start == 0 and o.mixed_switch == 1e-2
     L = gps.load()
     assert L.gps_set_radix_order(4) == gps.GPS_ERR_INVALID

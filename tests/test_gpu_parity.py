@@ -466,6 +466,26 @@ def test_nlpb_newton_surface_small(gps, ctx):
     assert err <= 1e-10, err
 
 
+def test_nlpb_forcing_rules(gps, ctx):
+    """Both inner-tolerance rules of the Newton outer loop (Eisenstat-Walker
+    choice 2, the default, and min(forcing, F/F0)) reach the oracle's
+    solution at the FP64 bar; they take different inner iterations."""
+    p = synth.workload(4, n=48, count=6, margin=5.0, kind="nlpb", conc=0.5)
+    el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+    ref, info = oracle.solve_nlpb(p.grid, p.rho, p.eps, p.electrolyte, p.eps0, tol=1e-11, max_iter=3000)
+    assert info["converged"]
+    iters = {}
+    for rule in (gps.GPS_FORCING_EW2, gps.GPS_FORCING_RATIO):
+        phi = T(np.zeros(p.grid.shape))
+        rep = ctx.pb_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), el, "nlpb", phi,
+                           gps.default_opts(tol_outer=1e-11, max_iter=3000, forcing_rule=rule))
+        assert rep.status == 0
+        err = rel2(N(phi, p.grid.shape), ref)
+        assert err <= 1e-10, (rule, err)
+        iters[rule] = rep.iters
+    assert iters[gps.GPS_FORCING_EW2] != iters[gps.GPS_FORCING_RATIO]
+
+
 def test_nlpb_printed_small_box(gps, ctx):
     """Algorithm 4 as printed (linear mixing) where it converges: a box
     smaller than the Debye length, weak source."""

@@ -162,7 +162,7 @@ def test_server_stream_identical_to_alone(gps, ctx):
     th = threading.Thread(target=producer)
     th.start()
     th.join()
-    results = [srv.wait(t) for t in tickets]
+    results = [srv.wait(t, timeout=300) for t in tickets]
     stats = srv.stats()
     srv.close()
     for (phi_a, rep_a), (_, _, phi_b), (status, rep_b) in zip(alone, keep, results):
@@ -217,7 +217,7 @@ def test_server_mixed_df64_stream_identical_to_alone(gps, ctx):
     th = threading.Thread(target=producer)
     th.start()
     th.join()
-    results = [srv.wait(t) for t in tickets]
+    results = [srv.wait(t, timeout=300) for t in tickets]
     stats = srv.stats()
     srv.close()
     for (phi_a, rep_a), (_, _, phi_b), (status, rep_b) in zip(alone, keep, results):
@@ -252,7 +252,7 @@ def test_server_admission_under_budget(gps):
         keep.append(phi)
         tickets.append(srv.submit(gps.make_request(gps.grid_from(p.grid), "gpe", rho, eps, phi),
                                   keep=(rho, eps, phi)))
-    out = [srv.wait(t) for t in tickets]
+    out = [srv.wait(t, timeout=300) for t in tickets]
     srv.close()
     assert all(s == 0 for s, _ in out)
     assert np.array_equal(keep[0], keep[2]) and np.array_equal(keep[1], keep[3])
@@ -261,6 +261,6 @@ def test_server_admission_under_budget(gps):
     eps = np.ascontiguousarray(a.eps.ravel())
     phi = np.zeros(a.grid.npts)
     t = tiny.submit(gps.make_request(gps.grid_from(a.grid), "gpe", rho, eps, phi), keep=(rho, eps, phi))
-    status, _ = tiny.wait(t)
+    status, _ = tiny.wait(t, timeout=300)
     tiny.close()
     assert status == gps.GPS_ERR_NOMEM

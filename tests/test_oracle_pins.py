@@ -364,6 +364,26 @@ def test_nlpb_alg4_matches_dense_newton(mode):
     assert np.linalg.norm(phi - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
+def test_nlpb_ew2_forcing_matches_dense_newton():
+    """Eisenstat-Walker forcing (choice 2) changes only how far each inner
+    solve goes: the same fixed point as the dense Newton solve of the
+    discrete system, on a source strong enough (potentials of several kT)
+    that the inner tolerances of the two forcing rules differ."""
+    g, rho, eps, el, e0 = _nl_problem()
+    rho = rho * 40.0
+    f = Fields(g, eps)
+    gam = pb.exclusion_from_eps(eps, e0)
+    ref, _ = dense.newton_nlpb(f, rho, gam, el)
+    assert np.abs(ref).max() > 3 * 9.5e-4           # strongly nonlinear (|phi| > 3 kT)
+    runs = {}
+    for rule in ("ratio", "ew2"):
+        phi, info = pb.alg4(g, rho, eps, el, e0, tol=1e-12, forcing=0.3, forcing_rule=rule)
+        assert info["converged"]
+        assert np.linalg.norm(phi - ref) <= 1e-10 * np.linalg.norm(ref)
+        runs[rule] = info["inner"]
+    assert runs["ratio"] != runs["ew2"]
+
+
 def test_nlpb_reduces_to_gpe_and_lpb():
     g, rho, eps, el, e0 = _nl_problem()
     gam = pb.exclusion_from_eps(eps, e0)
