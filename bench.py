@@ -306,12 +306,15 @@ def run_ours(args, ws, rank, local):
     ctx.close()
     del phi
     torch.cuda.empty_cache()
-    periodic128 = None if args.no_periodic128 else run_periodic128(gps, local, flush, args)
-    nonlinear = None if args.no_nonlinear else run_nonlinear(gps, local, flush)
-    comparison = None if args.no_comparison else run_comparison(gps, local, flush)
-    wire = None if args.no_wire else run_wire(gps, local, flush)
-    dft = None if args.no_dft else run_dft(gps, local, flush)
-    serving = None if args.no_serving else run_serving(gps, local, args)
+    # the other workloads' sections run on a single GPU only: under torchrun
+    # every rank solves the headline replica and nothing else
+    single = ws == 1
+    periodic128 = run_periodic128(gps, local, flush, args) if single and not args.no_periodic128 else None
+    nonlinear = run_nonlinear(gps, local, flush) if single and not args.no_nonlinear else None
+    comparison = run_comparison(gps, local, flush) if single and not args.no_comparison else None
+    wire = run_wire(gps, local, flush) if single and not args.no_wire else None
+    dft = run_dft(gps, local, flush) if single and not args.no_dft else None
+    serving = run_serving(gps, local, args) if single and not args.no_serving else None
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

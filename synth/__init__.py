@@ -21,6 +21,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
+import os
+
 import numpy as np
 from scipy.special import erf
 
@@ -123,6 +125,19 @@ def _axis_windows(grid: Grid, center, cutoff):
     return out
 
 
+def _window(iz, iy, ix):
+    """Index of a box given by per-axis index arrays: plain slices when every
+    array is a contiguous ascending range (the same elements, without the
+    gather and scatter of fancy indexing), else np.ix_."""
+    sl = []
+    for idx in (iz, iy, ix):
+        if len(idx) and idx[-1] - idx[0] + 1 == len(idx) and np.all(np.diff(idx) == 1):
+            sl.append(slice(int(idx[0]), int(idx[-1]) + 1))
+        else:
+            return np.ix_(iz, iy, ix)
+    return tuple(sl)
+
+
 def _gauss_profile(n, h, o, per, c, sigma, cutoff):
     """Index array and 1D Gaussian factor exp(-d^2/(2 sigma^2)) along one axis.
 
@@ -145,16 +160,22 @@ def _gauss_profile(n, h, o, per, c, sigma, cutoff):
     return idx, np.exp(-d * d / (2 * sigma * sigma))
 
 
-def add_gaussian(grid: Grid, field_: np.ndarray, q, sigma, center, cutoff_sigmas=10.0):
+def add_gaussian(grid: Grid, field_: np.ndarray, q, sigma, center, cutoff_sigmas=10.0, zrange=None):
     """Add a normalized Gaussian charge (total q) to `field_` in place; along
-    periodic axes the Gaussian is periodized (sum over images)."""
+    periodic axes the Gaussian is periodized (sum over images).  zrange =
+    (z0, z1): only the planes z0 <= k < z1 (the same values there)."""
     prof = [_gauss_profile(n, h, o, per, center[a], sigma, cutoff_sigmas * sigma)
             for a, (n, h, o, per) in enumerate(zip((grid.nx, grid.ny, grid.nz),
                                                    (grid.hx, grid.hy, grid.hz),
                                                    grid.origin, grid.periodic_axes()))]
     (ix, gx), (iy, gy), (iz, gz) = prof
+    if zrange is not None:
+        keep = (iz >= zrange[0]) & (iz < zrange[1])
+        iz, gz = iz[keep], gz[keep]
+        if not len(iz):
+            return
     norm = q * (2.0 * np.pi * sigma * sigma) ** -1.5
-    field_[np.ix_(iz, iy, ix)] += norm * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    field_[_window(iz, iy, ix)] += norm * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
 
 
 def switch_h(r, d0, delta):
@@ -169,7 +190,7 @@ def rigid_cavity(grid: Grid, spheres, delta, eps0=EPS_WATER):
         cutoff = d + 8.0 * delta         # h = 1 to double precision beyond
         (ix, dx), (iy, dy), (iz, dz) = _axis_windows(grid, c, cutoff)
         r = np.sqrt(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2)
-        prod[np.ix_(iz, iy, ix)] *= switch_h(r, d, delta)
+        prod[_window(iz, iy, ix)] *= switch_h(r, d, delta)
     return (eps0 - 1.0) * prod + 1.0
 
 
@@ -217,9 +238,25 @@ def _place(rng, grid, count, lo, hi, min_dist, max_tries=200000):
 
 
 def gaussian_charges(grid, charges):
+    """Sum of the Gaussian charges on the grid.  Large grids are filled by
+    threads over slabs of z planes; every point receives the same additions
+    in the same order as in a single pass, so the result does not depend on
+    the number of threads."""
     rho = np.zeros(grid.shape)
-    for q, sigma, c in charges:
-        add_gaussian(grid, rho, q, sigma, c)
+    nthreads = min(os.cpu_count() or 1, 16, grid.nz)
+    if grid.npts < (1 << 20) or nthreads < 2 or len(charges) < 2:
+        for q, sigma, c in charges:
+            add_gaussian(grid, rho, q, sigma, c)
+        return rho
+    from concurrent.futures import ThreadPoolExecutor
+    bounds = np.linspace(0, grid.nz, nthreads + 1).astype(int)
+
+    def slab(k):
+        for q, sigma, c in charges:
+            add_gaussian(grid, rho, q, sigma, c, zrange=(bounds[k], bounds[k + 1]))
+
+    with ThreadPoolExecutor(max_workers=nthreads) as ex:
+        list(ex.map(slab, range(nthreads)))
     return rho
 
 
