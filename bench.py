@@ -131,7 +131,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel from one
 # ncu capture, valid only for the kernel source it was taken with (the SHA-256
 # of the listed files, first 16 hex digits); otherwise the line reports null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # k_col<dfc, 512, 2, 1>, free 256^3: 796.9 MB read + 505.3 MB written per launch
+    "z_df64": {"bytes": 1302184960, "files": ['fft_col.cu', 'fft_common.cuh', 'device_util.cuh', 'gps_internal.h'], "sha": '1076a7d09e65df31'},
+}
 
 
 def source_sha(files):
@@ -310,6 +313,7 @@ def run_ours(args, ws, rank, local):
     # every rank solves the headline replica and nothing else
     single = ws == 1
     periodic128 = run_periodic128(gps, local, flush, args) if single and not args.no_periodic128 else None
+    configs13 = run_configs13(gps, local, flush) if single and not args.no_configs13 else None
     nonlinear = run_nonlinear(gps, local, flush) if single and not args.no_nonlinear else None
     comparison = run_comparison(gps, local, flush) if single and not args.no_comparison else None
     wire = run_wire(gps, local, flush) if single and not args.no_wire else None
@@ -326,6 +330,7 @@ def run_ours(args, ws, rank, local):
         "fp64": fp64,
         "e2e": e2e,
         "periodic128": periodic128,
+        "configs13": configs13,
         "nonlinear": nonlinear,
         "comparison": comparison,
         "wire": wire,
@@ -342,6 +347,56 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_configs13(gps, device, flush):
+    """Configurations 1 and 3: the free 64^3 single-cavity GPe (||r|| <= 1e-10)
+    and the surface-BC 160 x 160 x 256 slab with the linear and the nonlinear PB
+    term (1:1 electrolyte at 0.1 M, outer residual <= 1e-10), each on the plain
+    FP64 path and the mixed path (df64 spectrum, FP32 after the switch):
+    time of one solve after an untimed one, iterations, certificate, and the
+    mixed result's relative L2 difference from the FP64 one."""
+    import torch
+    import synth
+    out = {}
+    cases = (("1 gpe_free_64", synth.workload(1), "gpe"),
+             ("3 surface_lpb_160x160x256", synth.workload(3, kind="lpb"), "lpb"),
+             ("3 surface_nlpb_160x160x256", synth.workload(3, kind="nlpb"), "nlpb"))
+    ctx = gps.Context(device)
+    stream = torch.cuda.current_stream()
+    for name, p, kind in cases:
+        g = gps.grid_from(p.grid)
+        rho = torch.from_numpy(p.rho.ravel()).to(device)
+        eps = torch.from_numpy(p.eps.ravel()).to(device)
+        el = None
+        if kind != "gpe":
+            e = p.electrolyte
+            el = gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0)
+        row, phis = {}, {}
+        for prec_name, prec in (("fp64", gps.GPS_FP64), ("mixed_df64", gps.GPS_MIXED_DF64)):
+            o = gps.default_opts(tol_abs=1e-10, tol_outer=1e-10, max_iter=3000, precision=prec)
+            phi = torch.zeros_like(rho)
+
+            def solve():
+                phi.zero_()
+                if kind == "gpe":
+                    return ctx.gpe_solve(g, rho, eps, phi, o)
+                return ctx.pb_solve(g, rho, eps, el, kind, phi, o)
+
+            solve()
+            rep, ms = timed_call(stream, flush, solve)
+            phis[prec_name] = phi
+            row[prec_name] = {"ms": ms, "solves_per_s": 1e3 / ms, "pcg_iters": rep.iters,
+                              "outer_iters": rep.outer_iters, "status": rep.status,
+                              "grid_pt_iter_per_s": p.grid.npts * rep.iters / (ms / 1e3),
+                              "certificate": rep.fixed_point_res}
+        row["mixed_rel_l2_vs_fp64"] = (torch.linalg.norm(phis["mixed_df64"] - phis["fp64"]) /
+                                      torch.linalg.norm(phis["fp64"])).item()
+        row["speedup"] = row["fp64"]["ms"] / row["mixed_df64"]["ms"]
+        out[name] = row
+        del rho, eps, phis
+    ctx.close()
+    return out
 
 
 def run_periodic128(gps, device, flush, args):
@@ -1126,6 +1181,7 @@ def main():
     ap.add_argument("--no-nonlinear", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 solve of the headline")
     ap.add_argument("--no-periodic128", action="store_true")
+    ap.add_argument("--no-configs13", action="store_true", help="skip the configuration 1 and 3 section")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-comparison", action="store_true")
     ap.add_argument("--no-wire", action="store_true")

@@ -787,7 +787,7 @@ float time_launch(F&& launch, cudaStream_t st) {
   cudaEventSynchronize(e1);
   float warm = 0.f;
   cudaEventElapsedTime(&warm, e0, e1);
-  const int reps = warm > 1.0f ? 1 : 3;
+  const int reps = warm > 1.0f ? 1 : warm > 0.1f ? 3 : 7;
   float best = 1e30f;
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(e0, st);
@@ -859,12 +859,24 @@ void tune_spec(Shape& S, cudaStream_t st) {
     V* W = tmp.alloc<V>(wn);
     double* in = tmp.alloc<double>(S.n);
     double* outv = tmp.alloc<double>(S.n);
+    double* sc = tmp.alloc<double>(S.n);
+    float* sc32 = tmp.alloc<float>(S.n);
     ck(cudaMemsetAsync(in, 0, S.n * sizeof(double), st));
+    ck(cudaMemsetAsync(sc, 0, S.n * sizeof(double), st));
+    ck(cudaMemsetAsync(sc32, 0, S.n * sizeof(float), st));
     ck(cudaMemsetAsync(W, 0, wn * sizeof(V), st));
     Batch b{};
     PipeArgs a{};
+    // the arrays the PCG's passes read: scale factors (FP64 and the FP32
+    // copy) on both sides and r for (v, r), so that candidates are timed on
+    // the loads they will do
     a.in = in;
     a.out = outv;
+    a.in_scale = sc;
+    a.out_scale = sc;
+    a.in_scale32 = sc32;
+    a.out_scale32 = sc32;
+    a.dot_with = in;
     a.table = S.table;
     a.table32 = S.table32;
     a.tabledf = S.tabledf;
