@@ -229,7 +229,10 @@ __global__ void __launch_bounds__(kThreads) k_x_fwd(PassGeom g, FftSched s, cons
   double sum = 0.0;
   {
     constexpr int U = 4;
-    LineIter it(L);
+    // XH: the padded half (j >= nx = L/2) is never read -- the first stage
+    // runs on the lower half only (fft_lines prunes it) -- so only the data
+    // positions are staged
+    LineIter it(XH ? g.nx : L);
     while (it.l < nl) {
       T va[U], vb[U];
       int dst[U];
@@ -408,14 +411,17 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
   pair_offsets<V>(g, p0, nl, woff);
   __syncthreads();
   {
+    // Each stored value k < Hx is loaded once and gives both Z_k and, by
+    // Hermitian symmetry, Z_(L-k) = conj A_k + i conj B_k.
     constexpr int U = LoadBatch<V>::v / 2;
-    LineIter it(L);
+    LineIter it(g.Hx);
     while (it.l < nl) {
       V A[U], B[U];
-      int dst[U];
+      int dst[U], dstm[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         dst[u] = -1;
+        dstm[u] = -1;
         A[u] = czero<V>();
         B[u] = czero<V>();
         if (it.l < nl) {
@@ -423,22 +429,20 @@ __global__ void __launch_bounds__(kThreads) k_x_inv(PassGeom g, FftSched s, cons
           const bool hasb = 2 * (p0 + l) + 1 < g.nrows;
           const V* wa = W + woff[2 * l];
           const V* wb = W + woff[2 * l + 1];
-          if (k < g.Hx) {
-            A[u] = wa[k];
-            if (hasb) B[u] = wb[k];
-          } else {
-            const int m = L - k;
-            A[u] = cconj(wa[m]);
-            if (hasb) B[u] = cconj(wb[m]);
-          }
+          A[u] = wa[k];
+          if (hasb) B[u] = wb[k];
           if (k == 0 || 2 * k == L) { A[u].y = T(0); B[u].y = T(0); }   // DC and Nyquist are real
           dst[u] = l * ls + pidx<V>(k);
+          if (k > 0 && 2 * k < L) dstm[u] = l * ls + pidx<V>(L - k);
           it.next();
         }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (dst[u] >= 0) b0[dst[u]] = mk<V>(A[u].x - B[u].y, A[u].y + B[u].x);   // Z = A + i B
+        if (dst[u] >= 0) {
+          b0[dst[u]] = mk<V>(A[u].x - B[u].y, A[u].y + B[u].x);             // Z = A + i B
+          if (dstm[u] >= 0) b0[dstm[u]] = mk<V>(A[u].x + B[u].y, B[u].x - A[u].y);   // conj A + i conj B
+        }
     }
   }
   __syncthreads();
