@@ -574,7 +574,9 @@ struct Request {
   gps_request req;
   unsigned long long ticket = 0;
   double t0 = 0.0;
-  bool done = false;
+  // set by the engine's thread after rep and status; read by the threads
+  // that poll or wait on the ticket
+  std::atomic<bool> done{false};
   int status = GPS_PENDING;
   gps_report rep{};
 };
@@ -1700,6 +1702,9 @@ struct gps_server {
   bool stop = false;
   int fatal = GPS_OK;
   std::thread worker;
+  // engine figures for gps_server_stats, copied by the worker under mu
+  size_t stat_bytes = 0;
+  int stat_max_concurrent = 0;
 
   size_t busy() const {
     size_t b = eng.queue.size();
@@ -1744,8 +1749,17 @@ struct gps_server {
       for (auto& p : eng.pools) idle_pools &= p->busy() == 0;
       if (!failed && after > 0 && after == before && idle_pools)
         std::this_thread::sleep_for(std::chrono::milliseconds(1));   // queued work waiting for memory
-      if (!failed && eng.finished_total == done_before) continue;   // nothing to report
+      if (!failed && eng.finished_total == done_before) {   // nothing to report
+        std::unique_lock<std::mutex> lk(mu, std::try_to_lock);
+        if (lk.owns_lock()) {
+          stat_bytes = eng.bytes();
+          stat_max_concurrent = eng.max_concurrent;
+        }
+        continue;
+      }
       std::lock_guard<std::mutex> lk(mu);
+      stat_bytes = eng.bytes();
+      stat_max_concurrent = eng.max_concurrent;
       if (failed) {
         fatal = GPS_ERR_CUDA;
         for (auto& kv : reqs)
@@ -2172,7 +2186,7 @@ int gps_server_wait(gps_server* s, unsigned long long ticket, gps_report* rep) {
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return GPS_ERR_INVALID;
   Request* r = it->second.get();
-  s->done_cv.wait(lk, [&] { return r->done; });
+  s->done_cv.wait(lk, [&] { return r->done.load(); });
   if (rep) *rep = r->rep;
   const int st = r->status;
   s->reqs.erase(ticket);
@@ -2182,8 +2196,8 @@ int gps_server_wait(gps_server* s, unsigned long long ticket, gps_report* rep) {
 int gps_server_stats(gps_server* s, size_t* bytes, int* max_concurrent) {
   if (!s) return GPS_ERR_INVALID;
   std::lock_guard<std::mutex> lk(s->mu);
-  if (bytes) *bytes = s->eng.bytes();
-  if (max_concurrent) *max_concurrent = s->eng.max_concurrent;
+  if (bytes) *bytes = s->stat_bytes;
+  if (max_concurrent) *max_concurrent = s->stat_max_concurrent;
   return GPS_OK;
 }
 
