@@ -21,7 +21,7 @@ def _gen():
     return mod
 
 
-@pytest.mark.parametrize("case", ["surface"])
+@pytest.mark.parametrize("case", ["surface", "free"])
 def test_fixture_consistent(case):
     gen = _gen()
     wl, fname, _ = gen.CASES[case]

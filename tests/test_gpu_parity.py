@@ -828,13 +828,29 @@ def test_full_surface_nlpb(gps, ctx):
     assert _fixed_point_residual(p, ph, rions=rions) < 1e-10
 
 
+def test_full_free_union_nlpb_fp64(gps, ctx):
+    """Config 4 at full size (free 256^3, 200 charges in a union-of-spheres
+    cavity, nonlinear PB at 0.5 M), plain FP64 to an outer residual of 1e-11:
+    element-wise at 2049 sampled points, and in L2 norm and largest
+    magnitude, against the oracle's Algorithm 4 on the same inputs (stored
+    samples; same forcing rule, same outer residual)."""
+    p = synth.workload(4)
+    el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+    phi = T(np.zeros(p.grid.shape))
+    rep = ctx.pb_solve(gps.grid_from(p.grid), T(p.rho), T(p.eps), el, "nlpb", phi,
+                       gps.default_opts(tol_outer=1e-11, max_iter=4000, precision=gps.GPS_FP64))
+    assert rep.status == 0 and rep.outer_iters > 1
+    _check_golden(N(phi, p.grid.shape), "free_nlpb_256.txt", 1e-10)
+
+
 def test_full_free_union_nlpb_mixed(gps, ctx):
     """Config 4 at full size: free 256^3, 200 charges in a union-of-spheres
     cavity, nonlinear PB at 0.5 M, FP32 spectrum after the switch with the
     double-float spectrum as the high-precision side.  The FP64 certificate
     and the oracle's fixed-point residual of the full nonlinear equation are
     below 1e-8, and the result agrees with the plain FP64 solve (FP64
-    spectrum throughout) of the same problem to 1e-8."""
+    spectrum throughout) of the same problem to 1e-8, and with the oracle's
+    stored samples of the same problem to 1e-8."""
     p = synth.workload(4)
     el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
     g = gps.grid_from(p.grid)
@@ -851,6 +867,7 @@ def test_full_free_union_nlpb_mixed(gps, ctx):
     ph, ph_ref = N(phi, p.grid.shape), N(ref, p.grid.shape)
     err = rel2(ph, ph_ref)
     assert err <= 1e-8, err
+    _check_golden(ph, "free_nlpb_256.txt", 1e-8)
     gam = oracle.pb.exclusion_from_eps(p.eps, p.eps0)
     rions = oracle.pb.ionic_charge(ph, gam, p.electrolyte)
     assert _fixed_point_residual(p, ph, rions=rions) < 1e-8
