@@ -159,7 +159,12 @@ typedef struct {
                             final residual stands in for A phi_prev, so no operator is applied
                             (a warm start of Algorithm 2).  Every solve with warm_start set
                             keeps eps, phi and b - r on the device for the next one (three
-                            more grid-sized arrays in the context).  Otherwise a cold start. */
+                            more grid-sized arrays in the context).  Batched and served
+                            requests (gps_batch_solve, gps_server_submit): the same, from the
+                            last warm-start request of the same kind and electrolyte (compared
+                            by value) that completed in the pool of its grid, if that one was
+                            done when the request was admitted; the pool then keeps three
+                            more grid-sized arrays.  Otherwise a cold start (rep->warm 0). */
   int method;            /* gps_method (GPS_PCG) */
   double alpha;          /* GPS_PSD: fixed step length; 0 = steepest-descent step */
   int diis;              /* GPS_PSD: DIIS history length 0..GPS_MAX_DIIS (0 and 1: plain PSD) */

@@ -616,13 +616,16 @@ struct Pool {
   std::map<int, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   unsigned long long last_use = 0;
   bool in_flight = false;     // engine: a round was launched and not yet collected
-  // warm start (single-solve pools): eps, phi and b - r of the last solve
-  // that asked for it, and the flag of the same-eps test
+  // warm start: eps, phi and b - r of the last solve that asked for it (in
+  // an engine pool: the last such request that completed in it), and the
+  // flag of the same-eps test; ws_el (single solves) or ws_ion (engine
+  // pools) identifies its electrolyte
   double *ws_eps = nullptr, *ws_phi = nullptr, *ws_d = nullptr;
   int* ws_flag = nullptr;
   bool ws_valid = false;
   int ws_kind = -1;
   gps_electrolyte ws_el{};
+  IonParams ws_ion{};
   ScWork sc;
   double *dft_tmp = nullptr, *dft_part = nullptr;   // DFT-facing passes: scratch, partial sums
   DevMem mem;
@@ -647,6 +650,18 @@ size_t slot_bytes(const Shape& S) {
   const size_t wn = (size_t)S.Hp * S.Py * S.grid.nz;
   return 18 * S.n * sizeof(double) + S.n * sizeof(float) + wn * (sizeof(double2) + sizeof(float2)) +
          3 * 4096 * sizeof(double);
+}
+
+// Electrolyte parameters equal value by value (the warm-start test of
+// served requests, whose electrolyte arrays may live at other addresses).
+bool same_ion(const IonParams& a, const IonParams& b) {
+  if (a.nspecies != b.nspecies || a.steric != b.steric || a.inv_kt != b.inv_kt ||
+      a.inv_eps0m1 != b.inv_eps0m1 || a.exp_cap != b.exp_cap || a.lambda0 != b.lambda0)
+    return false;
+  for (int k = 0; k < a.nspecies && k < GPS_MAX_SPECIES; ++k)
+    if (a.zq[k] != b.zq[k] || a.zn[k] != b.zn[k] || a.z2n_kt[k] != b.z2n_kt[k] || a.a[k] != b.a[k])
+      return false;
+  return true;
 }
 
 std::unique_ptr<Pool> make_pool(std::shared_ptr<Shape> shape, int cap, bool own_stream) {
@@ -1171,7 +1186,61 @@ struct Engine {
       pools.erase(pools.begin() + victim);
     }
     pools.push_back(make_pool(shape, cap, true));
+    // warm starts of this pool's requests: INIT reads phi_0 and
+    // b_prev - r_prev from the slot's own phi and A p (see admit)
+    Fields& f = pools.back()->f;
+    f.wphi = f.phi;
+    f.wd = f.Ap;
     return pools.back().get();
+  }
+
+  // Warm start of a batched or served request (opts.warm_start; GPe and
+  // linear PB, as for single solves): from the pool's retained state -- eps,
+  // phi and b - r of the last warm-start request of the same kind and
+  // electrolyte that completed in this pool -- when the request's eps equals
+  // the retained one value by value.  phi_0 and b_prev - r_prev go into the
+  // slot's own phi and A p, where INIT reads them (engine pools have
+  // Fields wphi = phi, wd = Ap); nothing between admission and INIT writes
+  // either for these kinds.
+  static bool warm_request(const gps_request& q) {
+    return q.opts.warm_start && (q.kind == GPS_GPE || q.kind == GPS_LPB);
+  }
+
+  static bool warm_from_retained(Pool& P, int k, const SlotState& s) {
+    if (!P.ws_valid || P.ws_kind != s.kind || !same_ion(P.ws_ion, s.ion)) return false;
+    int differ = 1;
+    ck(cudaMemsetAsync(P.ws_flag, 0, sizeof(int), P.stream));
+    launch_eps_differ(P.f.eps + k * P.n, P.ws_eps, P.n, P.ws_flag, P.stream);
+    ck(cudaMemcpyAsync(&differ, P.ws_flag, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+    ck(cudaStreamSynchronize(P.stream));
+    if (differ) return false;
+    const size_t b = P.n * sizeof(double);
+    ck(cudaMemcpyAsync(P.f.phi + k * P.n, P.ws_phi, b, cudaMemcpyDeviceToDevice, P.stream));
+    ck(cudaMemcpyAsync(P.f.Ap + k * P.n, P.ws_d, b, cudaMemcpyDeviceToDevice, P.stream));
+    return true;
+  }
+
+  // Keeps slot k's finished warm-start request as the pool's retained state
+  // (three more fields of the pool's size; none if they cannot be had).
+  static void retain(Pool& P, int k, const SlotState& s) {
+    if (!P.ws_eps) {
+      try {
+        double* e = P.mem.alloc<double>(P.n);
+        double* f = P.mem.alloc<double>(P.n);
+        double* d = P.mem.alloc<double>(P.n);
+        int* fl = P.mem.alloc<int>(1);
+        P.ws_eps = e;
+        P.ws_phi = f;
+        P.ws_d = d;
+        P.ws_flag = fl;
+      } catch (std::bad_alloc&) {
+        return;   // what was allocated stays with the pool until it is freed
+      }
+    }
+    launch_warm_store(batch_of(P, PH_DONE, -1), P.f, k, P.ws_eps, P.ws_phi, P.ws_d, P.n, P.stream);
+    P.ws_valid = true;
+    P.ws_kind = s.kind;
+    P.ws_ion = s.ion;
   }
 
   void admit(Pool& P, Request* r) {
@@ -1183,6 +1252,7 @@ struct Engine {
     ck(cudaMemcpyAsync(P.f.rho + k * P.n, q.rho_host, b, cudaMemcpyHostToDevice, P.stream));
     ck(cudaMemcpyAsync(P.f.eps + k * P.n, q.eps_host, b, cudaMemcpyHostToDevice, P.stream));
     SlotState s = initial_state(q.kind, &q.el, q.opts);
+    if (warm_request(q) && warm_from_retained(P, k, s)) s.warm = 1;
     put_state(P, k, s, P.stream);
     P.has_nlpb |= q.kind == GPS_NLPB || q.kind == GPS_MPB;
     P.has_mixed |= s.mixed != 0;
@@ -1258,6 +1328,7 @@ struct Engine {
       if (s.phase != PH_DONE) continue;
       ck(cudaMemcpyAsync(r->req.phi_host, P.f.phi + k * P.n, P.n * sizeof(double),
                          cudaMemcpyDeviceToHost, P.stream));
+      if (warm_request(r->req) && (s.status == GPS_OK || s.status == GPS_ERR_NOT_CONVERGED)) retain(P, k, s);
       ck(cudaStreamSynchronize(P.stream));
       fill_report(&r->rep, s, r->t0);
       r->status = s.status;
@@ -1481,7 +1552,7 @@ int solve_direct(Pool& P, const double* rho, const double* eps, double* phi, int
     const int stt = P.st_host[0].status;
     P.ws_valid = stt == GPS_OK || stt == GPS_ERR_NOT_CONVERGED;
     if (P.ws_valid) {
-      launch_warm_store(batch_of(P, PH_DONE, -1), P.f, P.ws_eps, P.ws_phi, P.ws_d, P.n, st);
+      launch_warm_store(batch_of(P, PH_DONE, -1), P.f, 0, P.ws_eps, P.ws_phi, P.ws_d, P.n, st);
       P.ws_kind = kind;
       if (el) P.ws_el = *el;
     }

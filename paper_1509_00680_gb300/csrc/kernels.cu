@@ -843,23 +843,24 @@ void launch_eps_differ(const double* a, const double* b, size_t n, int* flag, cu
   k_eps_differ<<<grid_blocks(n, kT), kT, 0, st>>>(a, b, n, flag);
 }
 
-// State kept for the next warm start (slot 0): eps, phi and b - r with
-// b = -4 pi (rho - background).
-__global__ void k_warm_store(Batch b, Fields f, double* __restrict__ weps, double* __restrict__ wphi,
-                             double* __restrict__ wd, size_t n) {
-  const SlotState& S = b.st[0];
+// State kept for the next warm start, from slot `slot`: eps, phi and b - r
+// with b = -4 pi (rho - background).
+__global__ void k_warm_store(Batch b, Fields f, int slot, double* __restrict__ weps,
+                             double* __restrict__ wphi, double* __restrict__ wd, size_t n) {
+  const SlotState& S = b.st[slot];
   const double bg = S.background;
+  const size_t off = (size_t)slot * b.vstride;
   GRID_STRIDE(i, n) {
-    weps[i] = f.eps[i];
-    wphi[i] = f.phi[i];
-    wd[i] = -kFourPi * (f.rho[i] - bg) - f.r[i];
+    weps[i] = f.eps[off + i];
+    wphi[i] = f.phi[off + i];
+    wd[i] = -kFourPi * (f.rho[off + i] - bg) - f.r[off + i];
   }
 }
 
-void launch_warm_store(const Batch& b, const Fields& f, double* weps, double* wphi, double* wd,
+void launch_warm_store(const Batch& b, const Fields& f, int slot, double* weps, double* wphi, double* wd,
                        size_t n, cudaStream_t st) {
   count_launch();
-  k_warm_store<<<grid_blocks(n, kT), kT, 0, st>>>(b, f, weps, wphi, wd, n);
+  k_warm_store<<<grid_blocks(n, kT), kT, 0, st>>>(b, f, slot, weps, wphi, wd, n);
 }
 
 // Float and double-float copies of a Green's table, made once per shape.

@@ -23,7 +23,9 @@ struct Fields {
   double *rions, *rp, *fresh, *lam, *dphi, *src;   // Algorithm 4
   double *tmp;                           // certificate source
   float *s32;                            // eps^-1/2 rounded to float (FP32 spectrum passes)
-  const double *wphi, *wd;               // warm start: previous phi and b - r (slot 0 only)
+  const double *wphi, *wd;               // warm start: phi_0 and b_prev - r_prev at each slot's offset
+                                         // (single solves: the retained arrays, slot 0; engine pools:
+                                         // phi and Ap themselves, filled at admission)
   const double* gam;                     // ion-exclusion function given by the caller (slot 0
                                          // only); nullptr: the cavity function (eps-1)/(eps0-1)
 };
@@ -49,7 +51,7 @@ void launch_fp_source(const Batch& b, const Fields& f, size_t n, int nslots, cud
 void launch_fp_residual(const Batch& b, const Fields& f, size_t n, int periodic, int nslots,
                         cudaStream_t st);
 void launch_eps_differ(const double* a, const double* b, size_t n, int* flag, cudaStream_t st);
-void launch_warm_store(const Batch& b, const Fields& f, double* weps, double* wphi, double* wd,
+void launch_warm_store(const Batch& b, const Fields& f, int slot, double* weps, double* wphi, double* wd,
                        size_t n, cudaStream_t st);
 void launch_table_split(const double* t, float* t32, float2* tdf, size_t n, cudaStream_t st);
 void launch_ionic_charge(const double* phi, const double* eps, const double* gam, double* out, size_t n,

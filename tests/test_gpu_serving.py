@@ -264,3 +264,47 @@ def test_server_admission_under_budget(gps):
     status, _ = tiny.wait(t, timeout=300)
     tiny.close()
     assert status == gps.GPS_ERR_NOMEM
+
+
+@pytest.mark.parametrize("bc,kind", [(1, "gpe"), (2, "lpb"), (0, "gpe")])
+def test_server_warm_start(gps, bc, kind):
+    """opts.warm_start on served requests (GPe and linear PB): a request whose
+    eps equals, value by value, that of the last warm-start request completed
+    in its pool starts from that request's potential and final residual
+    (reported warm), needs fewer iterations than the same request served
+    cold, and reaches the cold result (relative L2 <= 1e-10, both to
+    ||r|| <= 1e-12 ||b||); a request that does not ask, and one with eps
+    changed anywhere, start cold."""
+    rng = np.random.default_rng(61 + bc)
+    p = synth.serving_request(rng, 32, bc, kind, h=0.45)
+    g = gps.grid_from(p.grid)
+    el = gps.make_electrolyte(p.electrolyte.z, p.electrolyte.c_molar, p.electrolyte.temperature, p.eps0)
+    rho1 = p.rho
+    rho2 = p.rho + 0.02 * np.roll(p.rho, 3, axis=2)
+    tol = 1e-12 * 4 * np.pi * np.linalg.norm(rho2)
+    srv = gps.Server(0, hbm_budget_bytes=4 << 30)
+    try:
+        def serve(rho, eps, warm):
+            rho_h = np.ascontiguousarray(rho.ravel())
+            eps_h = np.ascontiguousarray(eps.ravel())
+            phi = np.full(p.grid.npts, np.nan)
+            o = gps.default_opts(tol_abs=tol, max_iter=2000, warm_start=warm)
+            t = srv.submit(gps.make_request(g, kind, rho_h, eps_h, phi, el, o), keep=(rho_h, eps_h, phi))
+            status, rep = srv.wait(t, timeout=120)
+            assert status == 0
+            return phi, rep
+        _, r1 = serve(rho1, p.eps, 1)
+        assert r1.warm == 0
+        phi_w, r2 = serve(rho2, p.eps, 1)
+        assert r2.warm == 1
+        phi_c, r3 = serve(rho2, p.eps, 0)
+        assert r3.warm == 0
+        assert r2.iters < r3.iters
+        err = np.linalg.norm(phi_w - phi_c) / np.linalg.norm(phi_c)
+        assert err <= 1e-10, err
+        eps3 = p.eps.copy()
+        eps3.flat[123] *= 1.0 + 1e-9
+        _, r4 = serve(rho2, eps3, 1)
+        assert r4.warm == 0
+    finally:
+        srv.close()
