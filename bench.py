@@ -1168,6 +1168,69 @@ def cufft_comparison(torch, grid, P, steps):
     return res
 
 
+def run_warm_serving(args):
+    """Served warm starts (opts.warm_start): per BC and problem (GPe, linear
+    PB) at edge 64, h = 0.3, a sequence of requests that share eps while rho
+    drifts (rho_k = rho + 0.01 k roll(rho, 1 along z), as successive steps of
+    a fixed-cavity calculation), each submitted once the previous one has
+    completed, served cold and then with warm_start (from the pool's retained
+    eps, phi and b - r of the previous request).  Reports the mean PCG
+    iterations and latency of requests 1 .. K-1 both ways and the largest
+    relative L2 difference of a warm result from the cold one."""
+    from paper_1509_00680_gb300 import build
+    import synth
+
+    build.build()
+    from paper_1509_00680_gb300 import gps
+
+    K = max(2, args.warm_count)
+    srv = gps.Server(0, hbm_budget_bytes=8 << 30)
+    cases = {}
+    try:
+        for bc in (0, 1, 2):
+            for kind in ("gpe", "lpb"):
+                rng = np.random.default_rng(1200 + 2 * bc + (kind == "lpb"))
+                p = synth.serving_request(rng, 64, bc, kind)
+                e = p.electrolyte
+                el = gps.make_electrolyte(e.z, e.c_molar, e.temperature, p.eps0)
+                g = gps.grid_from(p.grid)
+                eps_h = np.ascontiguousarray(p.eps.ravel())
+                shifted = np.roll(p.rho, 1, axis=2)
+                rhos = [np.ascontiguousarray((p.rho + 0.01 * k * shifted).ravel()) for k in range(K)]
+                runs = {}
+                for warm in (0, 1):
+                    iters, ms, nwarm, phis = [], [], 0, []
+                    for k in range(K):
+                        phi = np.full(p.grid.npts, np.nan)
+                        o = gps.default_opts(tol_abs=1e-10, max_iter=2000, warm_start=warm)
+                        t = srv.submit(gps.make_request(g, kind, rhos[k], eps_h, phi, el, o),
+                                       keep=(rhos[k], eps_h, phi))
+                        status, rep = srv.wait(t, timeout=300)
+                        if status != 0:
+                            raise RuntimeError("warm-serving request failed with status %d" % status)
+                        if k > 0:
+                            iters.append(rep.iters)
+                            ms.append(rep.time_ms)
+                            nwarm += rep.warm
+                        phis.append(phi)
+                    runs[warm] = (iters, ms, nwarm, phis)
+                diff = max(float(np.linalg.norm(a - b) / np.linalg.norm(b))
+                           for a, b in zip(runs[1][3], runs[0][3]))
+                name = "%s_%s_64" % (("free", "periodic", "surface")[bc], kind)
+                cases[name] = {
+                    "cold": {"iters": statistics.mean(runs[0][0]), "ms": statistics.mean(runs[0][1])},
+                    "warm": {"iters": statistics.mean(runs[1][0]), "ms": statistics.mean(runs[1][1]),
+                             "started_warm": runs[1][2]},
+                    "max_rel_l2_warm_vs_cold": diff,
+                }
+                print("warm serving %s: cold %.1f iterations, warm %.1f" % (
+                    name, cases[name]["cold"]["iters"], cases[name]["warm"]["iters"]), file=sys.stderr, flush=True)
+    finally:
+        srv.close()
+    print(json.dumps({"mode": "warm_serving", "requests_per_sequence": K,
+                      "tol_abs": 1e-10, "cases": cases}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1204,12 +1267,18 @@ def main():
     ap.add_argument("--fp64-peak", action="store_true", help="measure the FP64 rate (cuBLAS DGEMM)")
     ap.add_argument("--cpu-configs", action="store_true",
                     help="time the CPU oracle on every configuration (median of 5)")
+    ap.add_argument("--warm-serving", action="store_true",
+                    help="served warm starts: sequences of requests sharing eps, cold against warm")
+    ap.add_argument("--warm-count", type=int, default=8, help="--warm-serving: requests per sequence")
     args = ap.parse_args()
     if args.fp64_peak:
         run_fp64_peak(args)
         return
     if args.cpu_configs:
         run_cpu_configs(args)
+        return
+    if args.warm_serving:
+        run_warm_serving(args)
         return
     if args.passes:
         run_passes(args)
