@@ -127,6 +127,13 @@ def peaks():
 # FP64 FMA units: 152 SMs x 2 DFMA/clk (measured 600 GFMA/s on this GPU, see
 # --fp64-peak) at the 2070 MHz maximum SM clock, 2 flop per FMA.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP32 issue rate: 152 SMs x 128 FP32 lanes x 2.07 GHz (an FMA is one instruction).
+FP32_PEAK_TINST = 152 * 128 * 2.070e9 / 1e12
+# FP32 instructions per double-float operation as the spectrum passes implement
+# them: an addition is the TwoSum of the high parts plus the sum of the low
+# parts (8), a product the TwoProd of the high parts by FMA plus the two cross
+# terms (4).
+DF64_ADD_INST, DF64_MUL_INST = 8, 4
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel from one
 # ncu capture, valid only for the kernel source it was taken with (the SHA-256
@@ -1040,6 +1047,26 @@ def vector_bytes(P, periodic=False):
     return {"update_p": (72 if periodic else 56) * n, "update_r": 48 * n}
 
 
+def df64_alu_view(base, ms, P):
+    """FP32-pipe view of a double-float spectrum pass, the bound its counters
+    show (issue-bound, FMA pipe the busiest): the conventional FFT flops of
+    kernel_flops split as in a radix-2 butterfly (6 additions and 4 products
+    per 10 flops) and the Green's-table products of the z pass, each costed
+    at the FP32 instructions of its double-float operation, over the launch
+    time, against the FP32 issue rate.  The conventional count exceeds what
+    radix-8 butterflies and the pruned zero half execute, so this is an upper
+    estimate of the pass's FP32 work rate."""
+    fl = kernel_flops(base, P)
+    table = 2.0 * P["Hx"] * P["Py"] * P["Pz"] if base == "z" else 0.0
+    inst = (fl - table) * (0.6 * DF64_ADD_INST + 0.4 * DF64_MUL_INST) + table * DF64_MUL_INST
+    ach = inst / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TINST, "unit": "T FP32 instructions/s",
+            "frac": ach / FP32_PEAK_TINST, "fp32_instructions": inst,
+            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2.07 GHz",
+            "model": "5 L log2 L flops per complex FFT, 0.6 x 8 + 0.4 x 4 FP32 instructions per flop; "
+                     "4 per Green's-table product"}
+
+
 def kernel_roofline(kind, ms, P, peaks_, periodic=False):
     """Roofline entry of one kernel kind from its average launch time."""
     hbm = peaks_.get("hbm_gbs")
@@ -1063,9 +1090,12 @@ def kernel_roofline(kind, ms, P, peaks_, periodic=False):
     if byt is None or not hbm:
         return {"kernel": kind, "avg_launch_ms": ms}
     ach = byt / (ms / 1e3) / 1e9
-    return {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm, "traffic": ncu_traffic(kind), "avg_launch_ms": ms,
-            "algorithmic_bytes": byt, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), burst"}
+    out = {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+           "frac": ach / hbm, "traffic": ncu_traffic(kind), "avg_launch_ms": ms,
+           "algorithmic_bytes": byt, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), burst"}
+    if prec == "df64" and base in ("x_fwd", "y_fwd", "z", "y_inv", "x_inv"):
+        out["alu_view"] = df64_alu_view(base, ms, P)
+    return out
 
 
 def run_passes(args):
