@@ -46,3 +46,13 @@ def test_alu_view_only_for_df64_passes(P):
     assert "alu_view" not in bench.kernel_roofline("z_fp32", 0.38, P, {"hbm_gbs": 6770.1})
     assert "alu_view" not in bench.kernel_roofline("update_p", 0.17, P, {"hbm_gbs": 6770.1})
     assert bench.kernel_roofline("z", 6.9, P, {"hbm_gbs": 6770.1})["bound"] == "alu"
+
+
+def test_config_is_the_workload_only():
+    """Both arms print config_dict() as `config` and report how they compute
+    beside it, so the two lines name the same workload."""
+    c = bench.config_dict()
+    assert c["workload"] == bench.WORKLOAD and c["grid"] == [256, 256, 256]
+    assert "precision" not in c and "pcg_iters_per_solve" not in c
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    assert src.count('"config": config_dict(), "precision": ') == 2
